@@ -1,0 +1,186 @@
+/*
+ * cbaa.h -- C ABI of libcbaa.so, the sm_103a (B300) implementation of the
+ * Cube of Bit Arrays Algorithm (CBAA) for super-host detection of Xu, Ding
+ * and Hu, "GPU based Real-time Super Hosts Detection at Distributed Edge
+ * Routers" (arXiv 1901.06207).
+ *
+ * Problem (Section III, Def. 1): in a time window, find every inner address
+ * iip whose number of distinct outer peers |OP(iip)| is at least theta, from
+ * <iip, oip> pairs seen at several edge routers, each router keeping a small
+ * local structure that a global server merges.
+ *
+ * Conventions for every call:
+ *  - Pointers named dev_* are CUDA device pointers (global memory of the
+ *    current device); host_* are host pointers.  The caller owns all of
+ *    them.  None of the calls below allocates device memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls marked "async" only enqueue work on it; calls marked
+ *    "sync" return after the stream reached the end of their work.
+ *  - Every call returns an int status (CBAA_OK = 0 or a negative error).
+ *    On an error nothing is enqueued unless stated otherwise.
+ *  - Calls are thread-safe as long as two calls never touch the same cube
+ *    or workspace concurrently.
+ *
+ * Cube memory format (the bytes a local server sends, Section III.C): uint32
+ * words.  With S = 2^r sketches, A = n_ra + n_va arrays, array a holding
+ * c_a = 2^cbn[a] columns of g = 2^log2_g bits and W = g/32 words per column:
+ *   word(cs, a, col, w) = cs*CSW + B_a + col*W + w,
+ *   B_a = sum_{b<a} c_b*W,  CSW = sum_a c_a*W,
+ * and row `row` of a column is bit (row % 32) of word (row / 32).
+ */
+#ifndef CBAA_H
+#define CBAA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CBAA_MAX_ARRAYS 8   /* |RA| + |VA| */
+#define CBAA_MAX_RA     6   /* |RA| */
+
+/* Status codes. */
+enum {
+    CBAA_OK                 = 0,
+    CBAA_ERR_INVALID_ARG    = -1,  /* bad geometry, null or misaligned pointer, short buffer */
+    CBAA_ERR_GEOMETRY       = -2,  /* merge of cubes with different parameters (Section III.C) */
+    CBAA_ERR_CAPACITY       = -3,  /* more hosts than the caller's output capacity */
+    CBAA_ERR_WORKSPACE      = -4,  /* candidate tuples or hosts exceeded the workspace */
+    CBAA_ERR_CUDA           = -5,  /* a CUDA runtime call failed */
+    CBAA_ERR_TIMEOUT        = -6,  /* a bounded device wait gave up */
+    CBAA_ERR_NO_DEVICE      = -7   /* no usable CUDA device */
+};
+
+/* Host-list flags. */
+#define CBAA_FLAG_SATURATED 1u     /* union column had no zero bit; estimate uses Z = 1 */
+
+/*
+ * Geometry of a cube (Section III.A/B).
+ *  r          CS selector width: the right (least significant) r bits of the
+ *             mangled address select one of S = 2^r sketches; 1 <= r <= 16.
+ *             The left part LP = mangled >> r has L = 32 - r bits.
+ *  n_ra/n_va  number of restoring / validating arrays; 2 <= n_ra <= 6,
+ *             n_ra + n_va <= 8.
+ *  log2_g     rows per column g = 2^log2_g, 7 <= log2_g <= 15.
+ *  cbn[a]     column-index width of array a (RA first, then VA); 5..16, and
+ *             <= L for RAs.
+ *  ring_off[i] (RA only) CL_bs(i) - r: CL(i) is cbn(i) consecutive bits of
+ *             LP starting at this offset, wrapping from the top of LP to
+ *             bit 0.  ring_off[0] = 0, strictly increasing, < L.  EP(i) runs
+ *             from ring_off[i] to ring_off[i+1] (cyclically),
+ *             |CP(i)| = cbn(i) - |EP(i)| >= 0 and |CP(i)| <= |EP(i+1)|
+ *             (Section III.B).
+ *  seed_*     seeds of the mangle (Section III.A), the row hash H_bv and the
+ *             VA column hashes H_j (Alg. 1).  All three are the bijective
+ *             32-bit finaliser x^=x>>16; x*=0x7feb352d; x^=x>>15;
+ *             x*=0x846ca68b; x^=x>>16 applied to (input ^ seed); rows and
+ *             VA columns take its top bits.
+ *  threshold_form 0: hot-column bound g(1-eps)e^{-theta/g} (Thm. 2 solved
+ *             for est >= theta); 1: the printed g(1+eps)e^{-theta/g} - g eps.
+ */
+typedef struct cbaa_params {
+    uint32_t r, n_ra, n_va, log2_g;
+    uint32_t cbn[CBAA_MAX_ARRAYS];
+    uint32_t ring_off[CBAA_MAX_ARRAYS];
+    uint32_t seed_mangle, seed_bv;
+    uint32_t seed_va[CBAA_MAX_ARRAYS];
+    uint32_t threshold_form;
+} cbaa_params;
+
+/* One detected super host (Alg. 3 output + Thm. 2 estimate). */
+typedef struct cbaa_host {
+    uint32_t ip;        /* restored, unmangled inner address */
+    uint32_t z_union;   /* zero bits of its union column UC(ip) (Def. 2) */
+    float    est;       /* -g ln(Z / (g - g eps)), Thm. 2 */
+    uint32_t flags;     /* CBAA_FLAG_* */
+} cbaa_host;
+
+/* Outcome of a detect, written to device memory by cbaa_detect_async. */
+typedef struct cbaa_detect_info {
+    int32_t  status;        /* CBAA_OK, CBAA_ERR_CAPACITY or CBAA_ERR_WORKSPACE */
+    uint32_t n_hosts;       /* hosts found (may exceed the output capacity) */
+    uint32_t n_hot;         /* hot columns over all CS and RAs (Alg. 2) */
+    uint32_t n_tuples;      /* partial tuples that passed the CP and union tests */
+    uint32_t need_tuples;   /* on CBAA_ERR_WORKSPACE: entries needed by the stage that overflowed */
+    uint32_t reserved[3];
+} cbaa_detect_info;
+
+typedef struct cbaa_cube cbaa_cube;   /* opaque handle: a params copy plus the caller's memory */
+
+/* Human-readable name of a status code.  Never returns NULL. */
+const char *cbaa_status_str(int status);
+
+/* Check a geometry against the rules above.  Host only, no device needed. */
+int cbaa_params_validate(const cbaa_params *p);
+
+/* Bytes of a cube with geometry p (0 if p is invalid).  Host only.
+ * Section V.C's setting (r=4, 3+1 arrays, g = c = 2^12) gives 128 MiB. */
+size_t cbaa_cube_bytes(const cbaa_params *p);
+
+/* Bytes of detect workspace for up to max_candidates partial tuples and
+ * hosts per stage (0 if p is invalid).  Host only. */
+size_t cbaa_detect_workspace_bytes(const cbaa_params *p, size_t max_candidates);
+
+/* Wrap caller memory as a cube and zero it (async).  dev_mem: >=
+ * cbaa_cube_bytes(p) bytes, 16-byte aligned, owned by the caller for the
+ * handle's lifetime.  *out receives a host-allocated handle. */
+int cbaa_cube_init(const cbaa_params *p, void *dev_mem, size_t bytes, cbaa_cube **out, void *stream);
+
+/* Free the handle (not the device memory).  NULL is accepted. */
+int cbaa_cube_destroy(cbaa_cube *cube);
+
+/* Device pointer of the cube words, and the geometry it was made with. */
+void *cbaa_cube_data(const cbaa_cube *cube);
+int cbaa_cube_params(const cbaa_cube *cube, cbaa_params *out);
+
+/* Zero every bit (async): the start of a new time window. */
+int cbaa_cube_reset(cbaa_cube *cube, void *stream);
+
+/* Alg. 1 (Section III.B), async: for each of n pairs {iip, oip} at
+ * dev_pairs (uint32[2n], 8-byte aligned; iip first) set bit H_bv(oip) in
+ * the |RA|+|VA| columns that the mangled iip selects in its CS.  Bits are
+ * only ever set, so any order of pairs and any concurrency give one cube.
+ * n = 0 is a no-op. */
+int cbaa_cube_update(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *stream);
+
+/* Section III.C merge, async: dst |= src_0 | ... | src_{k-1} word by word.
+ * All cubes must share dst's geometry (else CBAA_ERR_GEOMETRY); k = 0 is a
+ * no-op; dst may not be among srcs. */
+int cbaa_cube_merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream);
+
+/* Column statistics of the end-of-window pass, async (Eq. 1, Thm. 1 and the
+ * hot-column bound of Section III.C):
+ *   dev_zc   uint16[S][A][cmax]: zero bits of every column (cmax = max c_a;
+ *            entries past c_a are left untouched),
+ *   dev_za   uint64[S][A]: zero bits of every array,
+ *   dev_eps  double[S]: eps = prod_a (ones_a / (c_a g)), the measured
+ *            one-bit fraction standing in for Thm. 1's 1 - e^{-eta/(c g)},
+ *   dev_zmax int64[S]: floor of the hot-column bound for theta.
+ * Any of dev_zc, dev_eps, dev_zmax may be NULL; dev_za is required. */
+int cbaa_column_stats(const cbaa_cube *cube, uint32_t theta, uint16_t *dev_zc, uint64_t *dev_za,
+                      double *dev_eps, int64_t *dev_zmax, void *stream);
+
+/* Alg. 2 + Alg. 3 + Thm. 2 (Section III.C), async: restore every address
+ * whose union column has at most floor(theta_bn) zero bits, with its
+ * estimate, sorted by ip.  dev_ws: cbaa_detect_workspace_bytes(p, m) bytes
+ * (16-byte aligned) for some m; dev_out: room for cap records; dev_info:
+ * one cbaa_detect_info.  The first min(n_hosts, cap) records (smallest ips)
+ * are written.  Errors found on the device are reported in dev_info only. */
+int cbaa_detect_async(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_bytes,
+                      cbaa_host *dev_out, size_t cap, cbaa_detect_info *dev_info, void *stream);
+
+/* Same as cbaa_detect_async followed by the copy of the records to host_out
+ * (room for cap) and *n_out = number of hosts found; sync.  Returns
+ * CBAA_ERR_CAPACITY when n_hosts > cap (the first cap records are valid) and
+ * CBAA_ERR_WORKSPACE when the workspace was too small (*n_out then holds
+ * the tuple count the overflowing stage needed). */
+int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_bytes,
+                cbaa_host *host_out, size_t cap, size_t *n_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBAA_H */

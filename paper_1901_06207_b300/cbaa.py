@@ -1,0 +1,282 @@
+"""ctypes binding of libcbaa.so (argument marshalling only).
+
+Every step of the detector runs in the CUDA library; this module turns
+torch tensors (device memory, streams) into the pointers and sizes of the
+C ABI declared in include/cbaa.h and raises on error statuses.  There is no
+CPU fallback: if the library cannot be loaded, using this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcbaa.so")
+
+MAX_ARRAYS = 8
+MAX_RA = 6
+FLAG_SATURATED = 1
+
+OK, ERR_INVALID_ARG, ERR_GEOMETRY, ERR_CAPACITY, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("r", ctypes.c_uint32), ("n_ra", ctypes.c_uint32), ("n_va", ctypes.c_uint32), ("log2_g", ctypes.c_uint32),
+        ("cbn", ctypes.c_uint32 * MAX_ARRAYS), ("ring_off", ctypes.c_uint32 * MAX_ARRAYS),
+        ("seed_mangle", ctypes.c_uint32), ("seed_bv", ctypes.c_uint32),
+        ("seed_va", ctypes.c_uint32 * MAX_ARRAYS), ("threshold_form", ctypes.c_uint32),
+    ]
+
+
+class Host(ctypes.Structure):
+    _fields_ = [("ip", ctypes.c_uint32), ("z_union", ctypes.c_uint32), ("est", ctypes.c_float),
+                ("flags", ctypes.c_uint32)]
+
+
+class DetectInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_hosts", ctypes.c_uint32), ("n_hot", ctypes.c_uint32),
+                ("n_tuples", ctypes.c_uint32), ("need_tuples", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
+
+
+HOST_DTYPE = np.dtype([("ip", "<u4"), ("z", "<u4"), ("est", "<f4"), ("flags", "<u4")])
+assert HOST_DTYPE.itemsize == ctypes.sizeof(Host) == 16
+INFO_BYTES = ctypes.sizeof(DetectInfo)
+
+
+class CbaaError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def _signatures():
+    P, vp, sz = ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_size_t
+    return {
+        "cbaa_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+        "cbaa_params_validate": (ctypes.c_int, [P]),
+        "cbaa_cube_bytes": (sz, [P]),
+        "cbaa_detect_workspace_bytes": (sz, [P, sz]),
+        "cbaa_cube_init": (ctypes.c_int, [P, vp, sz, ctypes.POINTER(vp), vp]),
+        "cbaa_cube_destroy": (ctypes.c_int, [vp]),
+        "cbaa_cube_data": (vp, [vp]),
+        "cbaa_cube_params": (ctypes.c_int, [vp, P]),
+        "cbaa_cube_reset": (ctypes.c_int, [vp, vp]),
+        "cbaa_cube_update": (ctypes.c_int, [vp, vp, sz, vp]),
+        "cbaa_cube_merge": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.c_int, vp]),
+        "cbaa_column_stats": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp, vp, vp, vp]),
+        "cbaa_detect_async": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, sz, vp, vp]),
+        "cbaa_detect": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, sz, ctypes.POINTER(sz), vp]),
+        "cbaa_bench_red_or": (ctypes.c_int, [vp, sz, sz, ctypes.c_uint32, vp]),
+    }
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library with every entry point's argument types declared."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcbaa.so not built at {LIB_PATH}; run python -m paper_1901_06207_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _signatures().items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return lib().cbaa_status_str(status).decode()
+
+
+def _check(status: int, what: str) -> int:
+    if status != OK:
+        raise CbaaError(status, what)
+    return status
+
+
+# --------------------------------------------------------------------------- geometry
+
+def make_params(r: int, n_ra: int, n_va: int, log2_g: int, cbn, *, seed_mangle=0x3C6EF372,
+                seed_bv=0xA54FF53A, seed_va=(0x510E527F, 0x9B05688C, 0x1F83D9AB, 0x5BE0CD19),
+                threshold_form: int = 0) -> dict:
+    """Geometry dict with CL_bs offsets splitting LP as evenly as possible, larger EPs first."""
+    L = 32 - r
+    base, rem = divmod(L, n_ra)
+    ep = [base + 1] * rem + [base] * (n_ra - rem)
+    off = [0]
+    for e in ep[:-1]:
+        off.append(off[-1] + e)
+    cbn = list(cbn)
+    if len(cbn) == 1:
+        cbn = cbn * (n_ra + n_va)
+    sv = list(seed_va) + [0] * (MAX_ARRAYS - len(seed_va))
+    return dict(r=r, n_ra=n_ra, n_va=n_va, log2_g=log2_g, cbn=cbn + [0] * (MAX_ARRAYS - len(cbn)),
+                ring_off=off + [0] * (MAX_ARRAYS - len(off)), seed_mangle=seed_mangle, seed_bv=seed_bv,
+                seed_va=sv[:MAX_ARRAYS], threshold_form=threshold_form)
+
+
+def params(d: dict) -> Params:
+    p = Params()
+    p.r, p.n_ra, p.n_va, p.log2_g = d["r"], d["n_ra"], d["n_va"], d["log2_g"]
+    for k, v in enumerate(d["cbn"][:MAX_ARRAYS]):
+        p.cbn[k] = v
+    for k, v in enumerate(d["ring_off"][:MAX_ARRAYS]):
+        p.ring_off[k] = v
+    p.seed_mangle, p.seed_bv = d["seed_mangle"], d["seed_bv"]
+    for k, v in enumerate(d["seed_va"][:MAX_ARRAYS]):
+        p.seed_va[k] = v
+    p.threshold_form = d.get("threshold_form", 0)
+    return p
+
+
+def validate(d: dict) -> int:
+    return lib().cbaa_params_validate(ctypes.byref(params(d)))
+
+
+def cube_bytes(d: dict) -> int:
+    return int(lib().cbaa_cube_bytes(ctypes.byref(params(d))))
+
+
+def workspace_bytes(d: dict, max_candidates: int) -> int:
+    return int(lib().cbaa_detect_workspace_bytes(ctypes.byref(params(d)), max_candidates))
+
+
+# --------------------------------------------------------------------------- device objects
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int | None:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Workspace:
+    """Detect workspace: device bytes sized for ``max_candidates`` tuples/hosts per stage."""
+
+    def __init__(self, d: dict, max_candidates: int = 1 << 18, device="cuda"):
+        torch = _torch()
+        self.nbytes = workspace_bytes(d, max_candidates)
+        if self.nbytes == 0:
+            raise CbaaError(ERR_INVALID_ARG, "workspace size")
+        self.max_candidates = max_candidates
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+
+    @property
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+
+class Cube:
+    """A cube of bit arrays in caller (torch) device memory."""
+
+    def __init__(self, d: dict, device="cuda", memory=None, stream=None):
+        torch = _torch()
+        self.geometry = dict(d)
+        self._p = params(d)
+        _check(lib().cbaa_params_validate(ctypes.byref(self._p)), "params")
+        self.nbytes = cube_bytes(d)
+        if memory is None:
+            memory = torch.empty(self.nbytes // 4, dtype=torch.int32, device=device)
+        self.memory = memory
+        h = ctypes.c_void_p()
+        _check(lib().cbaa_cube_init(ctypes.byref(self._p), memory.data_ptr(), memory.numel() * memory.element_size(),
+                                    ctypes.byref(h), _stream_ptr(stream)), "cube_init")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.cbaa_cube_destroy(h)
+            self.handle = None
+
+    def to_numpy(self) -> np.ndarray:
+        """The cube words as a uint32 numpy array (synchronises, copies to host)."""
+        torch = _torch()
+        torch.cuda.synchronize()
+        return self.memory.view(torch.int32).cpu().numpy().view(np.uint32)
+
+    def reset(self, stream=None):
+        _check(lib().cbaa_cube_reset(self.handle, _stream_ptr(stream)), "cube_reset")
+
+    def update(self, pairs, n: int | None = None, stream=None):
+        """pairs: device uint32/int32 tensor of shape [n, 2] (iip, oip), contiguous."""
+        if n is None:
+            n = pairs.shape[0] if pairs.dim() == 2 else pairs.numel() // 2
+        _check(lib().cbaa_cube_update(self.handle, pairs.data_ptr(), n, _stream_ptr(stream)), "cube_update")
+
+    def update_ptr(self, ptr: int, n: int, stream=None):
+        _check(lib().cbaa_cube_update(self.handle, ptr, n, _stream_ptr(stream)), "cube_update")
+
+    def merge(self, others, stream=None):
+        arr = (ctypes.c_void_p * max(1, len(others)))(*[o.handle.value for o in others])
+        _check(lib().cbaa_cube_merge(self.handle, arr, len(others), _stream_ptr(stream)), "cube_merge")
+
+    def column_stats(self, theta: int, stream=None) -> dict:
+        torch = _torch()
+        g = self.geometry
+        S, A = 1 << g["r"], g["n_ra"] + g["n_va"]
+        cmax = max(1 << c for c in g["cbn"][:A])
+        dev = self.memory.device
+        zc = torch.zeros(S * A * cmax, dtype=torch.int16, device=dev)
+        za = torch.zeros(S * A, dtype=torch.int64, device=dev)
+        eps = torch.zeros(S, dtype=torch.float64, device=dev)
+        zmax = torch.zeros(S, dtype=torch.int64, device=dev)
+        _check(lib().cbaa_column_stats(self.handle, theta, zc.data_ptr(), za.data_ptr(), eps.data_ptr(),
+                                       zmax.data_ptr(), _stream_ptr(stream)), "column_stats")
+        torch.cuda.synchronize()
+        return {"zc": zc.cpu().numpy().view(np.uint16).reshape(S, A, cmax),
+                "za": za.cpu().numpy().view(np.uint64).reshape(S, A),
+                "eps": eps.cpu().numpy(), "zmax": zmax.cpu().numpy()}
+
+    def detect(self, theta: int, ws: Workspace | None = None, cap: int = 1 << 16, stream=None,
+               max_retries: int = 6) -> np.ndarray:
+        """Sync detect; grows the workspace and the output on WORKSPACE / CAPACITY."""
+        for _ in range(max_retries):
+            if ws is None:
+                ws = Workspace(self.geometry, device=self.memory.device)
+            out = (Host * max(1, cap))()
+            n = ctypes.c_size_t(0)
+            st = lib().cbaa_detect(self.handle, theta, ws.ptr, ws.nbytes, out, cap, ctypes.byref(n),
+                                   _stream_ptr(stream))
+            if st == ERR_WORKSPACE:
+                ws = Workspace(self.geometry, max_candidates=max(2 * ws.max_candidates, 2 * int(n.value)),
+                               device=self.memory.device)
+                continue
+            if st == ERR_CAPACITY:
+                cap = int(n.value)
+                continue
+            _check(st, "detect")
+            self.last_workspace = ws
+            return np.frombuffer(out, dtype=HOST_DTYPE, count=int(n.value)).copy()
+        raise CbaaError(ERR_WORKSPACE, "detect retries exhausted")
+
+    def detect_async(self, theta: int, ws: Workspace, out, info, stream=None):
+        """Enqueue a detect writing sorted hosts to device tensor ``out`` (int32 [cap*4]) and ``info``."""
+        cap = out.numel() * out.element_size() // 16
+        _check(lib().cbaa_detect_async(self.handle, theta, ws.ptr, ws.nbytes, out.data_ptr(), cap,
+                                       info.data_ptr(), _stream_ptr(stream)), "detect_async")
+
+
+def hosts_from_device(out, info) -> tuple[np.ndarray, dict]:
+    """Decode a detect_async result (device tensors) into a host array and the info dict."""
+    raw = info.cpu().numpy().view(np.uint8).tobytes()[:INFO_BYTES]
+    inf = DetectInfo.from_buffer_copy(raw)
+    d = {"status": inf.status, "n_hosts": inf.n_hosts, "n_hot": inf.n_hot, "n_tuples": inf.n_tuples,
+         "need_tuples": inf.need_tuples}
+    cap = out.numel() * out.element_size() // 16
+    n = min(inf.n_hosts, cap)
+    hosts = out.cpu().numpy().view(np.uint8).view(HOST_DTYPE)[:n].copy()
+    return hosts, d

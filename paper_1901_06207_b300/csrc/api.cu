@@ -1,0 +1,233 @@
+// C ABI of libcbaa.so: argument checks, geometry derivation, launches.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "cbaa_internal.cuh"
+#include "detect_layout.h"
+
+struct cbaa_cube {
+    cbaa_params p;
+    cbaa::Geo G;
+    uint32_t *data;
+    size_t bytes;
+};
+
+namespace cbaa {
+
+Geo make_geo(const cbaa_params &p) {
+    Geo G;
+    std::memset(&G, 0, sizeof G);
+    G.r = p.r;
+    G.L = 32u - p.r;
+    G.smask = (1u << p.r) - 1u;
+    G.n_ra = p.n_ra;
+    G.n_va = p.n_va;
+    G.A = p.n_ra + p.n_va;
+    G.log2_g = p.log2_g;
+    G.g = 1u << p.log2_g;
+    G.W = G.g / 32u;
+    G.form = p.threshold_form;
+    G.seed_m = p.seed_mangle;
+    G.seed_bv = p.seed_bv;
+    uint32_t base = 0;
+    for (uint32_t a = 0; a < G.A; ++a) {
+        G.cbn[a] = p.cbn[a];
+        G.arr_base[a] = base;
+        base += (1u << p.cbn[a]) * G.W;
+        if ((1u << p.cbn[a]) > G.cmax) G.cmax = 1u << p.cbn[a];
+    }
+    G.arr_base[G.A] = base;
+    G.cs_words = base;
+    G.cube_words = (uint64_t)base << p.r;
+    for (uint32_t i = 0; i < G.n_ra; ++i) {
+        G.ring_off[i] = p.ring_off[i];
+        G.ep[i] = (p.ring_off[(i + 1) % G.n_ra] + G.L - p.ring_off[i]) % G.L;
+        G.cp[i] = p.cbn[i] - G.ep[i];
+    }
+    for (uint32_t j = 0; j < G.n_va; ++j) G.seed_va[j] = p.seed_va[j];
+    return G;
+}
+
+}  // namespace cbaa
+
+using cbaa::Geo;
+
+namespace {
+
+int validate(const cbaa_params *p) {
+    if (!p) return CBAA_ERR_INVALID_ARG;
+    if (p->r < 1 || p->r > 16) return CBAA_ERR_INVALID_ARG;
+    if (p->n_ra < 2 || p->n_ra > CBAA_MAX_RA) return CBAA_ERR_INVALID_ARG;
+    if (p->n_ra + p->n_va > CBAA_MAX_ARRAYS) return CBAA_ERR_INVALID_ARG;
+    if (p->log2_g < 7 || p->log2_g > 15) return CBAA_ERR_INVALID_ARG;
+    if (p->threshold_form > 1) return CBAA_ERR_INVALID_ARG;
+    const uint32_t L = 32u - p->r, A = p->n_ra + p->n_va;
+    for (uint32_t a = 0; a < A; ++a) {
+        if (p->cbn[a] < 5 || p->cbn[a] > 16) return CBAA_ERR_INVALID_ARG;
+        if (a < p->n_ra && p->cbn[a] > L) return CBAA_ERR_INVALID_ARG;
+    }
+    if (p->ring_off[0] != 0) return CBAA_ERR_INVALID_ARG;
+    for (uint32_t i = 1; i < p->n_ra; ++i)
+        if (p->ring_off[i] <= p->ring_off[i - 1]) return CBAA_ERR_INVALID_ARG;
+    if (p->ring_off[p->n_ra - 1] >= L) return CBAA_ERR_INVALID_ARG;
+    uint32_t ep[CBAA_MAX_RA];
+    for (uint32_t i = 0; i < p->n_ra; ++i) ep[i] = (p->ring_off[(i + 1) % p->n_ra] + L - p->ring_off[i]) % L;
+    for (uint32_t i = 0; i < p->n_ra; ++i) {
+        if (p->cbn[i] < ep[i]) return CBAA_ERR_INVALID_ARG;                          // |CP(i)| >= 0
+        if (p->cbn[i] - ep[i] > ep[(i + 1) % p->n_ra]) return CBAA_ERR_INVALID_ARG;  // CP(i) inside EP(i+1)
+    }
+    uint64_t cs_words = 0;
+    for (uint32_t a = 0; a < A; ++a) cs_words += (uint64_t)(1u << p->cbn[a]) << (p->log2_g - 5);
+    if ((cs_words << p->r) >= (1ull << 32)) return CBAA_ERR_INVALID_ARG;   // 32-bit word offsets
+    return CBAA_OK;
+}
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char *cbaa_status_str(int status) {
+    switch (status) {
+        case CBAA_OK: return "ok";
+        case CBAA_ERR_INVALID_ARG: return "invalid argument";
+        case CBAA_ERR_GEOMETRY: return "geometry mismatch";
+        case CBAA_ERR_CAPACITY: return "output capacity exceeded";
+        case CBAA_ERR_WORKSPACE: return "workspace too small";
+        case CBAA_ERR_CUDA: return "CUDA error";
+        case CBAA_ERR_TIMEOUT: return "device wait timed out";
+        case CBAA_ERR_NO_DEVICE: return "no CUDA device";
+        default: return "unknown status";
+    }
+}
+
+int cbaa_params_validate(const cbaa_params *p) { return validate(p); }
+
+size_t cbaa_cube_bytes(const cbaa_params *p) {
+    if (validate(p) != CBAA_OK) return 0;
+    return (size_t)cbaa::make_geo(*p).cube_words * 4u;
+}
+
+size_t cbaa_detect_workspace_bytes(const cbaa_params *p, size_t max_candidates) {
+    if (validate(p) != CBAA_OK || max_candidates == 0 || max_candidates > (1ull << 31)) return 0;
+    return cbaa::ws_layout(cbaa::make_geo(*p), max_candidates).total;
+}
+
+int cbaa_cube_init(const cbaa_params *p, void *dev_mem, size_t bytes, cbaa_cube **out, void *stream) {
+    if (!out) return CBAA_ERR_INVALID_ARG;
+    *out = nullptr;
+    int st = validate(p);
+    if (st != CBAA_OK) return st;
+    const Geo G = cbaa::make_geo(*p);
+    if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 15u) || bytes < G.cube_words * 4u)
+        return CBAA_ERR_INVALID_ARG;
+    cbaa_cube *c = new (std::nothrow) cbaa_cube;
+    if (!c) return CBAA_ERR_INVALID_ARG;
+    c->p = *p;
+    c->G = G;
+    c->data = static_cast<uint32_t *>(dev_mem);
+    c->bytes = G.cube_words * 4u;
+    if (cudaMemsetAsync(c->data, 0, c->bytes, as_stream(stream)) != cudaSuccess) {
+        delete c;
+        return CBAA_ERR_CUDA;
+    }
+    *out = c;
+    return CBAA_OK;
+}
+
+int cbaa_cube_destroy(cbaa_cube *cube) {
+    delete cube;
+    return CBAA_OK;
+}
+
+void *cbaa_cube_data(const cbaa_cube *cube) { return cube ? cube->data : nullptr; }
+
+int cbaa_cube_params(const cbaa_cube *cube, cbaa_params *out) {
+    if (!cube || !out) return CBAA_ERR_INVALID_ARG;
+    *out = cube->p;
+    return CBAA_OK;
+}
+
+int cbaa_cube_reset(cbaa_cube *cube, void *stream) {
+    if (!cube) return CBAA_ERR_INVALID_ARG;
+    return cudaMemsetAsync(cube->data, 0, cube->bytes, as_stream(stream)) == cudaSuccess ? CBAA_OK : CBAA_ERR_CUDA;
+}
+
+int cbaa_cube_update(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *stream) {
+    if (!cube) return CBAA_ERR_INVALID_ARG;
+    if (n == 0) return CBAA_OK;
+    if (!dev_pairs || (reinterpret_cast<uintptr_t>(dev_pairs) & 7u)) return CBAA_ERR_INVALID_ARG;
+    return cbaa::launch_update(cube->G, cube->data, dev_pairs, n, as_stream(stream)) == cudaSuccess ? CBAA_OK
+                                                                                                    : CBAA_ERR_CUDA;
+}
+
+int cbaa_cube_merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream) {
+    if (!dst || k < 0 || (k > 0 && !srcs)) return CBAA_ERR_INVALID_ARG;
+    if (k == 0) return CBAA_OK;
+    const uint32_t *ptrs[64];
+    for (int k0 = 0; k0 < k; k0 += 64) {
+        const int kk = (k - k0) < 64 ? (k - k0) : 64;
+        for (int j = 0; j < kk; ++j) {
+            const cbaa_cube *s = srcs[k0 + j];
+            if (!s || s == dst) return CBAA_ERR_INVALID_ARG;
+            if (std::memcmp(&s->p, &dst->p, sizeof(cbaa_params)) != 0) return CBAA_ERR_GEOMETRY;
+            ptrs[j] = s->data;
+        }
+        if (cbaa::launch_merge(dst->data, ptrs, kk, dst->G.cube_words, as_stream(stream)) != cudaSuccess)
+            return CBAA_ERR_CUDA;
+    }
+    return CBAA_OK;
+}
+
+int cbaa_column_stats(const cbaa_cube *cube, uint32_t theta, uint16_t *dev_zc, uint64_t *dev_za, double *dev_eps,
+                      int64_t *dev_zmax, void *stream) {
+    if (!cube || !dev_za) return CBAA_ERR_INVALID_ARG;
+    const double E = std::exp(-((double)theta / (double)cube->G.g));
+    return cbaa::launch_column_stats(cube->G, cube->data, dev_zc, dev_za, dev_eps, dev_zmax, E, as_stream(stream)) ==
+                   cudaSuccess
+               ? CBAA_OK
+               : CBAA_ERR_CUDA;
+}
+
+int cbaa_detect_async(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_bytes, cbaa_host *dev_out,
+                      size_t cap, cbaa_detect_info *dev_info, void *stream) {
+    if (!cube || !dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u) || !dev_info || (cap > 0 && !dev_out))
+        return CBAA_ERR_INVALID_ARG;
+    return cbaa::detect_enqueue(cube->G, cube->data, theta, dev_ws, ws_bytes, dev_out, cap, dev_info,
+                                cbaa::num_sms(), as_stream(stream));
+}
+
+int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_bytes, cbaa_host *host_out, size_t cap,
+                size_t *n_out, void *stream) {
+    if (!cube || !dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u) || !n_out || (cap > 0 && !host_out))
+        return CBAA_ERR_INVALID_ARG;
+    *n_out = 0;
+    cudaStream_t s = as_stream(stream);
+    cbaa::WsLayout Ly;
+    if (!cbaa::ws_layout_fit(cube->G, ws_bytes, &Ly)) return CBAA_ERR_WORKSPACE;
+    const cbaa::WsPtrs P = cbaa::ws_pointers(cube->G, Ly, dev_ws);
+    int st = cbaa::detect_enqueue(cube->G, cube->data, theta, dev_ws, ws_bytes, nullptr, 0, nullptr,
+                                  cbaa::num_sms(), s);
+    if (st != CBAA_OK) return st;
+    cbaa_detect_info info;
+    if (cudaMemcpyAsync(&info, &P.state->info, sizeof info, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CBAA_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CBAA_ERR_CUDA;
+    if (info.status == CBAA_ERR_WORKSPACE) {
+        *n_out = info.need_tuples;
+        return CBAA_ERR_WORKSPACE;
+    }
+    *n_out = info.n_hosts;
+    const size_t nw = info.n_hosts < cap ? info.n_hosts : cap;
+    if (nw > 0) {
+        if (cudaMemcpyAsync(host_out, P.sorted, nw * sizeof(cbaa_host), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return CBAA_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return CBAA_ERR_CUDA;
+    }
+    return info.n_hosts > cap ? CBAA_ERR_CAPACITY : CBAA_OK;
+}
+
+}  // extern "C"

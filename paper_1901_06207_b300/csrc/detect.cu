@@ -1,0 +1,303 @@
+// End-of-window restoration (Section III.C): Alg. 2 hot columns, Alg. 3
+// tuple checks, Thm. 2 estimates, for sm_103a.
+//
+// The paper tests every tuple of the product HC(0) x ... x HC(|RA|-1).  Here
+// the tuples are built one RA at a time instead, which reaches the same set:
+//  * HC(i) for i >= 1 is stored grouped by its low |CP(i-1)| bits, so the
+//    only candidates for position i after a partial tuple ending in hc_{i-1}
+//    are one bucket: those whose first bits equal CP(i-1) of hc_{i-1}
+//    (Alg. 3 step 1, applied as soon as both columns are known);
+//  * a partial tuple is dropped as soon as the AND of its columns has more
+//    than Zmax zero bits: adding columns to an AND only adds zeros, so such
+//    a tuple's union column could never pass Alg. 3 step 4.
+// The last stage closes the ring (CP(last) against the first bits of
+// hc_0), concatenates the EPs into LP (step 2), ANDs in the VA columns
+// H_j(LP) (step 3) and keeps LP when the union has at most Zmax zeros
+// (step 4).  One warp owns one partial tuple and holds its running AND in
+// registers (g/32 words spread over 32 lanes), so no union-column buffer
+// pool is needed.
+#include <cmath>
+
+#include "cbaa_internal.cuh"
+#include "detect_layout.h"
+
+namespace cbaa {
+
+namespace {
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) { return __reduce_add_sync(0xffffffffu, v); }
+
+// ---------------------------------------------------------------------------
+// Alg. 2.  Block (cs, i) lists the columns of RA i of sketch cs with no more
+// than Zmax zero bits.  For i = 0 the hot columns become the seed tuples
+// (cs, hc_0) of the join; for i >= 1 they are stored key-major (key = low
+// |CP(i-1)| bits) with bucket offsets.
+__global__ void __launch_bounds__(256) k_hot_lists(const Geo G, WsPtrs P) {
+    const uint32_t cs = blockIdx.x, i = blockIdx.y;
+    const uint32_t ncol = 1u << G.cbn[i];
+    const int64_t zm = P.zmax[cs];
+    const uint32_t kb = (i == 0) ? 0u : G.cp[i - 1];
+    const uint32_t jb = G.cbn[i] - kb;
+    const uint16_t *zc = P.zc + ((size_t)cs * G.A + i) * G.cmax;
+    uint16_t *list = P.hc + ((size_t)cs * G.n_ra + i) * P.hc_stride;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+
+    __shared__ uint32_t warp_tot[8], warp_off[8], s_base, s_count;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+
+    for (uint32_t p0 = 0; p0 < ncol; p0 += blockDim.x) {
+        const uint32_t p = p0 + threadIdx.x;
+        uint32_t col = 0;
+        bool hot = false;
+        if (p < ncol) {
+            col = ((p & ((1u << jb) - 1u)) << kb) | (p >> jb);
+            hot = (int64_t)zc[col] <= zm;
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, hot);
+        if (lane == 0) warp_tot[warp] = __popc(b);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = 0;
+            for (uint32_t w = 0; w < blockDim.x / 32; ++w) { warp_off[w] = run; run += warp_tot[w]; }
+            s_base = s_count;
+            s_count += run;
+            if (i == 0 && run > 0) s_base = atomicAdd(&P.state->stage_count[0], run);
+        }
+        __syncthreads();
+        if (hot) {
+            const uint32_t pos = s_base + warp_off[warp] + __popc(b & ((1u << lane) - 1u));
+            if (i == 0) {
+                if (pos < P.m) {
+                    Tuple t;
+                    t.cs = (uint16_t)cs;
+                    t.hc[0] = (uint16_t)col;
+                    P.tup[0][pos] = t;
+                }
+            } else {
+                list[pos] = (uint16_t)col;
+            }
+        }
+        __syncthreads();
+    }
+    const uint32_t n = s_count;
+    if (threadIdx.x == 0) {
+        P.nhc[(size_t)cs * G.n_ra + i] = n;
+        if (n) atomicAdd(&P.state->info.n_hot, n);
+    }
+    if (i == 0) return;
+    __syncthreads();   // the list written above is visible to the whole block
+    uint32_t *offs = P.boff + ((size_t)cs * G.n_ra + i) * P.boff_stride;
+    const uint32_t nkeys = 1u << kb, kmask = nkeys - 1u;
+    if (n == 0) {
+        for (uint32_t k = threadIdx.x; k <= nkeys; k += blockDim.x) offs[k] = 0;
+        return;
+    }
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const uint32_t key = list[t] & kmask;
+        const int64_t prev = (t == 0) ? -1 : (int64_t)(list[t - 1] & kmask);
+        for (int64_t k = prev + 1; k <= (int64_t)key; ++k) offs[k] = t;
+        if (t == n - 1)
+            for (uint32_t k = key + 1; k <= nkeys; ++k) offs[k] = n;
+    }
+}
+
+// Words of one column held by a lane: WPL consecutive words for g >= 1024,
+// else lane < W holds word `lane`.
+template <int WPL>
+__device__ __forceinline__ void load_col(const uint32_t *__restrict__ colp, uint32_t W, uint32_t lane, uint32_t (&v)[WPL]) {
+    if (WPL >= 4) {
+        const uint4 *p4 = reinterpret_cast<const uint4 *>(colp + lane * WPL);
+#pragma unroll
+        for (int k = 0; k < WPL / 4; ++k) {
+            const uint4 q = p4[k];
+            v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+        }
+    } else if (WPL == 2) {
+        const uint2 q = reinterpret_cast<const uint2 *>(colp)[lane];
+        v[0] = q.x; v[WPL - 1] = q.y;
+    } else {
+        v[0] = (lane < W) ? colp[lane] : 0xFFFFFFFFu;
+    }
+}
+
+// Join stage s (1 <= s < |RA|): extend each partial tuple (cs, hc_0..hc_{s-1})
+// by the hot columns of RA s in its CP bucket.
+template <int WPL>
+__global__ void __launch_bounds__(256) k_join(const Geo G, const uint32_t *__restrict__ cube, WsPtrs P, uint32_t s) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const bool last = (s == G.n_ra - 1);
+    const uint32_t cnt_in = P.state->stage_count[s - 1];
+    const uint32_t n_in = cnt_in < P.m ? cnt_in : P.m;
+    const Tuple *__restrict__ in = P.tup[(s - 1) & 1];
+    Tuple *__restrict__ out = P.tup[s & 1];
+    const bool lane_live = (WPL > 1) || lane < G.W;
+
+    for (uint32_t t = gw; t < n_in; t += nw) {
+        const Tuple tu = in[t];
+        const uint32_t cs = tu.cs;
+        const int64_t zm = P.zmax[cs];
+        uint32_t acc[WPL];
+#pragma unroll
+        for (int k = 0; k < WPL; ++k) acc[k] = 0xFFFFFFFFu;
+        for (uint32_t i = 0; i < s; ++i) {
+            uint32_t v[WPL];
+            load_col<WPL>(cube + col_word0(G, cs, i, tu.hc[i]), G.W, lane, v);
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) acc[k] &= v[k];
+        }
+        const uint32_t key = (uint32_t)tu.hc[s - 1] >> G.ep[s - 1];
+        const uint32_t *offs = P.boff + ((size_t)cs * G.n_ra + s) * P.boff_stride;
+        const uint16_t *list = P.hc + ((size_t)cs * G.n_ra + s) * P.hc_stride;
+        const uint32_t b0 = offs[key], b1 = offs[key + 1];
+        // LP bits already fixed by the EPs of hc_0 .. hc_{s-1}
+        uint32_t lp_part = 0;
+        if (last)
+            for (uint32_t i = 0; i < s; ++i) lp_part |= ((uint32_t)tu.hc[i] & ((1u << G.ep[i]) - 1u)) << G.ring_off[i];
+        const uint32_t close_bits = (uint32_t)tu.hc[0] & ((1u << G.cp[s]) - 1u);
+
+        for (uint32_t e = b0; e < b1; ++e) {
+            const uint32_t col = list[e];
+            if (last && (col >> G.ep[s]) != close_bits) continue;     // ring closure (Alg. 3 step 1)
+            uint32_t v[WPL];
+            load_col<WPL>(cube + col_word0(G, cs, s, col), G.W, lane, v);
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) v[k] &= acc[k];
+            uint32_t lp = 0;
+            if (last) {
+                lp = lp_part | ((col & ((1u << G.ep[s]) - 1u)) << G.ring_off[s]);   // step 2
+                for (uint32_t j = 0; j < G.n_va; ++j) {                               // step 3
+                    uint32_t w[WPL];
+                    load_col<WPL>(cube + col_word0(G, cs, G.n_ra + j, va_col(G, j, lp)), G.W, lane, w);
+#pragma unroll
+                    for (int k = 0; k < WPL; ++k) v[k] &= w[k];
+                }
+            }
+            uint32_t ones = 0;
+            if (lane_live) {
+#pragma unroll
+                for (int k = 0; k < WPL; ++k) ones += __popc(v[k]);
+            }
+            ones = warp_sum(ones);
+            const uint32_t zeros = G.g - ones;
+            if ((int64_t)zeros > zm || lane != 0) continue;                     // step 4
+            if (!last) {
+                const uint32_t slot = atomicAdd(&P.state->stage_count[s], 1u);
+                if (slot < P.m) {
+                    Tuple o = tu;
+                    o.hc[s] = (uint16_t)col;
+                    out[slot] = o;
+                }
+            } else {
+                const uint32_t slot = atomicAdd(&P.state->info.n_hosts, 1u);
+                if (slot < P.m) {
+                    // Thm. 2 estimate; Z = 0 is reported with Z = 1 and flagged.
+                    const double g = (double)G.g;
+                    const double eps = P.eps[cs];
+                    const uint32_t zs = zeros ? zeros : 1u;
+                    const double den = __dsub_rn(g, __dmul_rn(g, eps));
+                    double est = __dmul_rn(-g, log(__ddiv_rn((double)zs, den)));
+                    if (est < 0.0) est = 0.0;
+                    cbaa_host h;
+                    h.ip = unmangle(G, (lp << G.r) | cs);
+                    h.z_union = zeros;
+                    h.est = (float)est;
+                    h.flags = zeros ? 0u : CBAA_FLAG_SATURATED;
+                    P.hosts[slot] = h;
+                }
+            }
+        }
+    }
+}
+
+// Sort the restored hosts by ip (bitonic network over (ip << 32 | index)
+// keys, in shared memory up to kSmemKeys keys, else in the workspace),
+// write the first min(n, cap) to `out`, and settle the status.
+constexpr uint32_t kSmemKeys = 4096;
+
+__global__ void __launch_bounds__(1024) k_sort_out(const Geo G, WsPtrs P, cbaa_host *__restrict__ out, uint64_t cap) {
+    __shared__ unsigned long long skeys[kSmemKeys];
+    DevState *st = P.state;
+    const uint32_t found = st->info.n_hosts;
+    const uint32_t n = found < P.m ? found : P.m;
+    uint32_t N = 1;
+    while (N < n) N <<= 1;
+    unsigned long long *keys = (N <= kSmemKeys) ? skeys : P.keys;
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
+        keys[k] = (k < n) ? (((unsigned long long)P.hosts[k].ip << 32) | k) : ~0ull;
+    __syncthreads();
+    for (uint32_t size = 2; size <= N; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t t = threadIdx.x; t < N / 2; t += blockDim.x) {
+                const uint32_t lo = 2 * t - (t & (stride - 1));
+                const uint32_t hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = keys[lo], b = keys[hi];
+                if ((a > b) == up) { keys[lo] = b; keys[hi] = a; }
+            }
+            __syncthreads();
+        }
+    }
+    const uint64_t nw = n < cap ? n : cap;
+    for (uint32_t k = threadIdx.x; k < nw; k += blockDim.x)
+        out[k] = P.hosts[keys[k] & 0xFFFFFFFFull];
+    if (threadIdx.x == 0) {
+        uint32_t need = 0, tuples = 0;
+        for (uint32_t s = 0; s + 1 < G.n_ra; ++s) {
+            const uint32_t c = st->stage_count[s];
+            tuples += c;
+            if (c > P.m && c > need) need = c;
+        }
+        if (found > P.m && found > need) need = found;
+        st->info.n_tuples = tuples;
+        st->info.need_tuples = need;
+        st->info.status = need ? CBAA_ERR_WORKSPACE : (found > cap ? CBAA_ERR_CAPACITY : CBAA_OK);
+    }
+}
+
+template <int WPL>
+cudaError_t launch_join(const Geo &G, const uint32_t *cube, const WsPtrs &P, uint32_t s, unsigned blocks, cudaStream_t st) {
+    k_join<WPL><<<blocks, 256, 0, st>>>(G, cube, P, s);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws, size_t ws_bytes,
+                   cbaa_host *out, uint64_t cap, cbaa_detect_info *info_copy, int num_sms, cudaStream_t s) {
+    WsLayout Ly;
+    if (!ws_layout_fit(G, ws_bytes, &Ly)) return CBAA_ERR_WORKSPACE;
+    WsPtrs P = ws_pointers(G, Ly, ws);
+    const double E = std::exp(-((double)theta / (double)G.g));
+
+    cudaError_t e = cudaMemsetAsync(P.state, 0, sizeof(DevState), s);
+    if (e != cudaSuccess) return CBAA_ERR_CUDA;
+    e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s);
+    if (e != cudaSuccess) return CBAA_ERR_CUDA;
+    k_hot_lists<<<dim3(G.smask + 1, G.n_ra), 256, 0, s>>>(G, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
+    const unsigned blocks = (unsigned)num_sms * 4;
+    const uint32_t wpl = G.W >= 32 ? G.W / 32 : 1;
+    for (uint32_t st = 1; st < G.n_ra; ++st) {
+        switch (wpl) {
+            case 1: e = launch_join<1>(G, cube, P, st, blocks, s); break;
+            case 2: e = launch_join<2>(G, cube, P, st, blocks, s); break;
+            case 4: e = launch_join<4>(G, cube, P, st, blocks, s); break;
+            case 8: e = launch_join<8>(G, cube, P, st, blocks, s); break;
+            case 16: e = launch_join<16>(G, cube, P, st, blocks, s); break;
+            default: e = launch_join<32>(G, cube, P, st, blocks, s); break;
+        }
+        if (e != cudaSuccess) return CBAA_ERR_CUDA;
+    }
+    k_sort_out<<<1, 1024, 0, s>>>(G, P, out ? out : P.sorted, out ? cap : P.m);
+    if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
+    if (info_copy) {
+        e = cudaMemcpyAsync(info_copy, &P.state->info, sizeof(cbaa_detect_info), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return CBAA_ERR_CUDA;
+    }
+    return CBAA_OK;
+}
+
+}  // namespace cbaa

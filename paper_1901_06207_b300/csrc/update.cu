@@ -1,0 +1,253 @@
+// Alg. 1 (cube update), the OR merge of Section III.C, and the column
+// statistics of the end-of-window pass (zero counts, Thm. 1 eps, the
+// hot-column bound) for sm_103a.
+//
+// Update design: the cube is written only by single-bit ORs (Alg. 1 never
+// reads it), so every bit set is a fire-and-forget reduction (RED.OR) that
+// is executed in L2 without a round trip.  The packet stream (8 B per pair)
+// is read with 128-bit loads marked evict-first so that it does not push
+// the cube out of L2; the cube itself is left with the default policy and
+// stays L2-resident when it fits.
+#include "cbaa_internal.cuh"
+
+namespace cbaa {
+
+namespace {
+
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p) {
+    uint4 v;
+    asm volatile("ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
+    asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// One IP pair through Alg. 1.  NRA/NVA > 0 fix the array counts at compile
+// time (the common 3+1 layout); 0 reads them from G.
+template <int NRA, int NVA>
+__device__ __forceinline__ void apply_pair(const Geo &G, uint32_t *__restrict__ cube, uint32_t iip, uint32_t oip) {
+    const uint32_t nra = NRA ? NRA : G.n_ra;
+    const uint32_t nva = NRA ? NVA : G.n_va;
+    const uint32_t row = row_of(G, oip);
+    const uint32_t m = mangle(G, iip);
+    const uint32_t cs = m & G.smask;            // right r bits select the CS
+    const uint32_t lp = m >> G.r;               // left 32 - r bits
+    const uint32_t bit = 1u << (row & 31u);
+    uint32_t *base = cube + (size_t)cs * G.cs_words + (row >> 5);
+#pragma unroll
+    for (uint32_t i = 0; i < (NRA ? NRA : CBAA_MAX_RA); ++i) {
+        if (NRA == 0 && i >= nra) break;
+        red_or(base + G.arr_base[i] + ra_col(G, i, lp) * G.W, bit);
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < (NRA ? NVA : CBAA_MAX_ARRAYS); ++j) {
+        if (NRA == 0 && j >= nva) break;
+        red_or(base + G.arr_base[nra + j] + va_col(G, j, lp) * G.W, bit);
+    }
+}
+
+// Grid-stride over 16-byte pairs-of-pairs; each thread keeps U loads in
+// flight before issuing their 2*U*A reductions.  Thread 0 of block 0 also
+// takes the unaligned head pair and the odd tail pair.
+template <int NRA, int NVA, int U>
+__global__ void __launch_bounds__(256) k_update(const Geo G, uint32_t *__restrict__ cube,
+                                                const uint32_t *__restrict__ pairs, uint64_t n) {
+    const uint64_t head = ((reinterpret_cast<uintptr_t>(pairs) & 15u) != 0 && n > 0) ? 1 : 0;
+    const uint4 *body = reinterpret_cast<const uint4 *>(pairs + 2 * head);
+    const uint64_t n2 = (n - head) / 2;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+
+    if (tid == 0) {
+        if (head) apply_pair<NRA, NVA>(G, cube, pairs[0], pairs[1]);
+        if ((n - head) & 1) {
+            const uint64_t t = n - 1;
+            apply_pair<NRA, NVA>(G, cube, pairs[2 * t], pairs[2 * t + 1]);
+        }
+    }
+    uint64_t i = tid;
+    for (; i + (U - 1) * stride < n2; i += U * stride) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ld_stream(body + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            apply_pair<NRA, NVA>(G, cube, v[u].x, v[u].y);
+            apply_pair<NRA, NVA>(G, cube, v[u].z, v[u].w);
+        }
+    }
+    for (; i < n2; i += stride) {
+        const uint4 v = ld_stream(body + i);
+        apply_pair<NRA, NVA>(G, cube, v.x, v.y);
+        apply_pair<NRA, NVA>(G, cube, v.z, v.w);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Merge: dst |= OR of up to kMaxSrc sources per launch, 128-bit words.
+
+constexpr int kMaxSrc = 16;
+struct SrcList {
+    const uint4 *p[kMaxSrc];
+    int k;
+};
+
+__global__ void __launch_bounds__(256) k_merge(uint4 *__restrict__ dst, const SrcList L, uint64_t n16) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        uint4 a = dst[i];
+        for (int k = 0; k < L.k; ++k) {
+            const uint4 b = ld_stream(L.p[k] + i);
+            a.x |= b.x; a.y |= b.y; a.z |= b.z; a.w |= b.w;
+        }
+        dst[i] = a;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Zero counts.  Block (cs*A + a, split) walks a slice of array a of sketch
+// cs; TPC threads share one column (TPC = min(W/4, 32)), each summing the
+// popcounts of its 16-byte pieces, then the TPC lanes reduce by shuffles.
+// One atomic per block adds the slice's zeros to za[cs][a].
+
+__global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t *__restrict__ cube,
+                                                     uint16_t *__restrict__ zc,
+                                                     unsigned long long *__restrict__ za, uint32_t splits) {
+    const uint32_t arr = blockIdx.x;                 // cs*A + a
+    const uint32_t cs = arr / G.A, a = arr % G.A;
+    const uint32_t ncol = 1u << G.cbn[a];
+    const uint32_t c0 = (uint32_t)(((uint64_t)ncol * blockIdx.y) / splits);
+    const uint32_t c1 = (uint32_t)(((uint64_t)ncol * (blockIdx.y + 1)) / splits);
+    const uint32_t q = G.W / 4;                      // 16-byte pieces per column
+    const uint32_t tpc = q < 32 ? q : 32;
+    const uint32_t per = q / tpc;                    // pieces per thread
+    const uint32_t sub = threadIdx.x % tpc;
+    const uint32_t cols_per_iter = blockDim.x / tpc;
+    const uint4 *arr4 = reinterpret_cast<const uint4 *>(cube + (size_t)cs * G.cs_words + G.arr_base[a]);
+
+    unsigned long long acc = 0;
+    for (uint32_t base = c0; base < c1; base += cols_per_iter) {
+        const uint32_t col = base + threadIdx.x / tpc;
+        uint32_t ones = 0;
+        if (col < c1) {
+            const uint4 *c4 = arr4 + (size_t)col * q;
+            for (uint32_t k = 0; k < per; ++k) {
+                const uint4 v = c4[sub + k * tpc];
+                ones += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+        }
+        for (uint32_t off = tpc >> 1; off > 0; off >>= 1) ones += __shfl_xor_sync(0xffffffffu, ones, off);
+        if (col < c1 && sub == 0) {
+            const uint32_t zeros = G.g - ones;
+            if (zc) zc[(size_t)arr * G.cmax + col] = (uint16_t)zeros;
+            acc += zeros;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    __shared__ unsigned long long part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += part[w];
+        atomicAdd(&za[arr], t);
+    }
+}
+
+// Thm. 1 with measured one-bit fractions, then the hot-column bound.  Each
+// operation is a correctly rounded IEEE double operation in a fixed order
+// (explicit _rn intrinsics, so nothing is contracted into an FMA).
+__global__ void k_eps_zmax(const Geo G, const unsigned long long *__restrict__ za, double E,
+                           double *__restrict__ eps_out, int64_t *__restrict__ zmax_out) {
+    const uint32_t cs = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cs > G.smask) return;
+    double eps = 1.0;
+    for (uint32_t a = 0; a < G.A; ++a) {
+        const unsigned long long bits = (unsigned long long)(1u << G.cbn[a]) << G.log2_g;
+        const unsigned long long ones = bits - za[(size_t)cs * G.A + a];
+        const double p1 = __ddiv_rn(__ull2double_rn(ones), __ull2double_rn(bits));
+        eps = __dmul_rn(eps, p1);
+    }
+    const double g = (double)G.g;
+    double t;
+    if (G.form == 1) {
+        const double b = __dmul_rn(__dmul_rn(g, __dadd_rn(1.0, eps)), E);
+        t = __dsub_rn(b, __dmul_rn(g, eps));
+    } else {
+        t = __dmul_rn(__dmul_rn(g, __dsub_rn(1.0, eps)), E);
+    }
+    if (eps_out) eps_out[cs] = eps;
+    if (zmax_out) zmax_out[cs] = (int64_t)floor(t);
+}
+
+}  // namespace
+
+static int g_num_sms = 0;
+
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    return g_num_sms;
+}
+
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_update(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    constexpr int U = 2;
+    const uint64_t n2 = n / 2 + 1;
+    uint64_t want = (n2 + 255) / 256;
+    const uint64_t cap = (uint64_t)num_sms() * 8;    // 8 x 256 threads per SM
+    const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+    if (G.n_ra == 3 && G.n_va == 1)
+        k_update<3, 1, U><<<blocks, 256, 0, s>>>(G, cube, pairs, n);
+    else
+        k_update<0, 0, U><<<blocks, 256, 0, s>>>(G, cube, pairs, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint64_t words, cudaStream_t s) {
+    const uint64_t n16 = words / 4;
+    const uint64_t cap = (uint64_t)num_sms() * 8;
+    uint64_t want = (n16 + 255) / 256;
+    const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+    for (int k0 = 0; k0 < k; k0 += kMaxSrc) {
+        SrcList L;
+        L.k = (k - k0) < kMaxSrc ? (k - k0) : kMaxSrc;
+        for (int j = 0; j < L.k; ++j) L.p[j] = reinterpret_cast<const uint4 *>(srcs[k0 + j]);
+        k_merge<<<blocks, 256, 0, s>>>(reinterpret_cast<uint4 *>(dst), L, n16);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc, uint64_t *za,
+                                double *eps, int64_t *zmax, double E, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(za, 0, sizeof(uint64_t) * (size_t)(G.smask + 1) * G.A, s);
+    if (e != cudaSuccess) return e;
+    const uint32_t arrays = (G.smask + 1) * G.A;
+    // Enough blocks to cover every SM several times; each slice is whole columns.
+    uint32_t splits = 1;
+    while ((uint64_t)arrays * splits < (uint64_t)num_sms() * 8 && splits < 64) splits <<= 1;
+    const uint32_t min_cols = 1u << 5;   // cbn >= 5 for every array
+    if (splits > min_cols) splits = min_cols;
+    k_zero_counts<<<dim3(arrays, splits), 256, 0, s>>>(G, cube, zc, reinterpret_cast<unsigned long long *>(za), splits);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (eps || zmax) {
+        const uint32_t S = G.smask + 1;
+        k_eps_zmax<<<(S + 127) / 128, 128, 0, s>>>(G, reinterpret_cast<const unsigned long long *>(za), E, eps, zmax);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace cbaa

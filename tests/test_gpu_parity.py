@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA path against the CPU oracle on the same seeded inputs.
+
+Bar: cubes, per-column zero counts, Zmax and host lists (ip, Z, flags) are
+bit-exact; eps is the same IEEE double; FP32 estimates agree to a relative
+1e-6 (both sides evaluate Thm. 2 in double and round once to float).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import geometries as GEO
+from paper_1901_06207_b300 import traffic as T
+
+pytestmark = pytest.mark.gpu
+EST_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1901_06207_b300 import build
+    build.build()
+    from paper_1901_06207_b300 import cbaa
+    return cbaa
+
+
+def dev_pairs(pairs: np.ndarray):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def tiny_window(seed, n=1 << 16, planted=40, lo=150, hi=600, hosts=2000, bg_max=60):
+    spec = T.TrafficSpec(n_packets=n, n_hosts=hosts, n_planted=planted, planted_lo=lo, planted_hi=hi,
+                         planted_dist="uniform", bg_mode="per_host", zipf_a=1.2, bg_max=bg_max, seed=seed)
+    return T.make_window(spec)
+
+
+def assert_hosts_equal(got: np.ndarray, want: np.ndarray):
+    assert got.size == want.size, (got.size, want.size)
+    assert np.array_equal(got["ip"], want["ip"])
+    assert np.array_equal(got["z"], want["z"])
+    assert np.array_equal(got["flags"], want["flags"])
+    w = want["est"].astype(np.float64)
+    g = got["est"].astype(np.float64)
+    assert np.all(np.abs(g - w) <= EST_RTOL * np.maximum(np.abs(w), 1.0)), np.max(np.abs(g - w))
+
+
+WINDOWS = {
+    "tiny": lambda: tiny_window(31, n=1 << 18, planted=300, lo=150, hi=700, hosts=3000, bg_max=64),
+    "tiny_sat": lambda: tiny_window(32, n=1 << 18, planted=200, lo=600, hi=3000, hosts=3000, bg_max=64),
+    "1m": lambda: T.make_window(T.spec_window_1m()),
+    "4m": lambda: T.make_window(T.spec_window_64m(scale_shift=4)),
+}
+_cache = {}
+
+
+def window(name):
+    if name not in _cache:
+        _cache[name] = WINDOWS[name]()
+    return _cache[name]
+
+
+CUBE_CASES = [("TINY", "tiny"), ("TINY2", "tiny"), ("PAPER", "1m"), ("L2", "4m"), ("SERVE", "4m"),
+              ("UNDERSIZED", "4m")]
+
+
+@pytest.mark.parametrize("geo,win", CUBE_CASES)
+def test_update_cube_bit_exact(C, oracle, geo, win):
+    d = GEO.ALL[geo]
+    w = window(win)
+    cube = C.Cube(d)
+    cube.update(dev_pairs(w.pairs))
+    got = cube.to_numpy()
+    want = oracle.build_cube(d, w.pairs)
+    assert np.array_equal(got, want)
+
+
+def test_update_ragged_and_unaligned(C, oracle):
+    """Odd counts, a start that is only 8-byte aligned, empty and one-pair calls, uneven batches."""
+    import torch
+    d = GEO.TINY2
+    w = window("tiny")
+    p = dev_pairs(w.pairs)
+    cube = C.Cube(d)
+    cube.update(p, n=0)
+    assert not cube.to_numpy().any()
+    bounds = [0, 1, 2, 5, 1000, 1001, 4097, 70001, w.pairs.shape[0]]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        cube.update_ptr(p.data_ptr() + 8 * a, b - a)        # start is 8-byte aligned at odd a
+    torch.cuda.synchronize()
+    assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
+
+
+def test_update_order_and_duplicates(C):
+    d = GEO.TINY
+    w = window("tiny")
+    c1, c2 = C.Cube(d), C.Cube(d)
+    c1.update(dev_pairs(w.pairs))
+    perm = np.random.default_rng(3).permutation(w.pairs.shape[0])
+    c2.update(dev_pairs(np.concatenate([w.pairs[perm], w.pairs[::7]])))
+    assert np.array_equal(c1.to_numpy(), c2.to_numpy())
+
+
+@pytest.mark.parametrize("k", [1, 3, 20])
+def test_merge_equals_union(C, oracle, k):
+    """Section III.C: OR of per-router cubes equals the cube of all the traffic (k > 16 spans launches)."""
+    d = GEO.TINY2
+    w = window("tiny")
+    rid, _ = T.split_by_router(w.pairs, 77, k)
+    routers = []
+    for i in range(k):
+        c = C.Cube(d)
+        c.update(dev_pairs(w.pairs[rid == i]))
+        routers.append(c)
+    dst = C.Cube(d)
+    dst.merge(routers)
+    assert np.array_equal(dst.to_numpy(), oracle.build_cube(d, w.pairs))
+
+
+def test_merge_geometry_mismatch(C):
+    a, b = C.Cube(GEO.TINY), C.Cube(GEO.with_form(GEO.TINY, 1))
+    with pytest.raises(C.CbaaError) as e:
+        a.merge([b])
+    assert e.value.status == C.ERR_GEOMETRY
+    with pytest.raises(C.CbaaError):
+        a.merge([a])
+
+
+@pytest.mark.parametrize("geo,win,theta,form", [("TINY", "tiny", 128, 0), ("TINY2", "tiny", 128, 1),
+                                                ("PAPER", "1m", 1024, 0), ("L2", "4m", 1024, 0),
+                                                ("L2", "4m", 1024, 1), ("UNDERSIZED", "4m", 1024, 0)])
+def test_column_stats_bit_exact(C, oracle, geo, win, theta, form):
+    d = GEO.with_form(GEO.ALL[geo], form)
+    w = window(win)
+    cube = C.Cube(d)
+    cube.update(dev_pairs(w.pairs))
+    st = cube.column_stats(theta)
+    host = oracle.build_cube(d, w.pairs)
+    zc, za = oracle.zero_counts(d, host)
+    A = d["n_ra"] + d["n_va"]
+    for a in range(A):
+        c = 1 << d["cbn"][a]
+        assert np.array_equal(st["zc"][:, a, :c].astype(np.uint32), zc[:, a, :c])
+    assert np.array_equal(st["za"], za)
+    E = oracle.exp_factor(theta, d["log2_g"])
+    for cs in range(1 << d["r"]):
+        e = oracle.eps(d, za, cs)
+        assert st["eps"][cs] == e                          # same IEEE double
+        assert st["zmax"][cs] == oracle.zmax(d, e, E)
+
+
+DETECT_CASES = [("TINY", "tiny", 128, 0), ("TINY", "tiny", 96, 1), ("TINY", "tiny_sat", 128, 0),
+                ("TINY2", "tiny", 128, 0), ("PAPER", "1m", 1024, 0), ("PAPER", "1m", 1024, 1),
+                ("L2", "4m", 1024, 0), ("L2", "4m", 700, 1), ("UNDERSIZED", "4m", 1024, 0),
+                ("SERVE", "4m", 1024, 0)]
+
+
+@pytest.mark.parametrize("geo,win,theta,form", DETECT_CASES)
+def test_detect_host_list_parity(C, oracle, geo, win, theta, form):
+    d = GEO.with_form(GEO.ALL[geo], form)
+    w = window(win)
+    cube = C.Cube(d)
+    cube.update(dev_pairs(w.pairs))
+    got = cube.detect(theta)
+    want = oracle.detect(d, oracle.build_cube(d, w.pairs), theta)["hosts"]
+    assert_hosts_equal(got, want)
+    assert np.all(np.diff(got["ip"].astype(np.int64)) > 0)       # sorted, no duplicates
+    if win == "tiny_sat":
+        assert (got["flags"] & C.FLAG_SATURATED).any()
+
+
+def test_detect_empty_cube_and_repeat(C):
+    d = GEO.PAPER
+    cube = C.Cube(d)
+    assert cube.detect(1024).size == 0
+    w = window("1m")
+    cube.update(dev_pairs(w.pairs))
+    a = cube.detect(1024)
+    b = cube.detect(1024)
+    assert a.size >= 20 and np.array_equal(a, b)
+
+
+def test_detect_capacity_returns_smallest_ips(C):
+    d = GEO.PAPER
+    w = window("1m")
+    cube = C.Cube(d)
+    cube.update(dev_pairs(w.pairs))
+    full = cube.detect(1024)
+    ws = C.Workspace(d)
+    out = (C.Host * 5)()
+    n = ctypes.c_size_t(0)
+    st = C.lib().cbaa_detect(cube.handle, 1024, ws.ptr, ws.nbytes, out, 5, ctypes.byref(n), None)
+    assert st == C.ERR_CAPACITY and n.value == full.size
+    got = np.frombuffer(out, dtype=C.HOST_DTYPE, count=5)
+    assert np.array_equal(got, full[:5])
+
+
+def test_detect_saturated_cube_reports_workspace(C):
+    """Every column hot: the tuple space explodes and detect says how much it needed, without faulting."""
+    import torch
+    d = GEO.TINY
+    cube = C.Cube(d)
+    cube.memory.fill_(-1)
+    ws = C.Workspace(d, max_candidates=1 << 12)
+    out = (C.Host * 16)()
+    n = ctypes.c_size_t(0)
+    st = C.lib().cbaa_detect(cube.handle, 128, ws.ptr, ws.nbytes, out, 16, ctypes.byref(n), None)
+    torch.cuda.synchronize()
+    assert st == C.ERR_WORKSPACE and n.value > (1 << 12)
+
+
+def test_detect_async_matches_sync(C):
+    import torch
+    d = GEO.L2
+    w = window("4m")
+    cube = C.Cube(d)
+    cube.update(dev_pairs(w.pairs))
+    sync = cube.detect(1024)
+    ws = C.Workspace(d)
+    out = torch.zeros(4 * 4096, dtype=torch.int32, device="cuda")
+    info = torch.zeros(8, dtype=torch.int32, device="cuda")
+    cube.detect_async(1024, ws, out, info)
+    hosts, inf = C.hosts_from_device(out, info)
+    assert inf["status"] == C.OK and inf["n_hosts"] == sync.size
+    assert np.array_equal(hosts, sync)
+
+
+def test_full_size_64m_window(C, oracle):
+    """The benchmark's workload: 64M packets into the 64 MiB L2-resident cube, launched as the bench does."""
+    d = GEO.L2
+    w = T.make_window(T.spec_window_64m())
+    cube = C.Cube(d)
+    cube.update(dev_pairs(w.pairs))
+    got_cube = cube.to_numpy()
+    want_cube = oracle.build_cube(d, w.pairs)
+    assert np.array_equal(got_cube, want_cube)
+    got = cube.detect(1024)
+    want = oracle.detect(d, want_cube, 1024)["hosts"]
+    assert_hosts_equal(got, want)
+    assert set(w.planted_ips.tolist()) <= set(got["ip"].tolist())
