@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""CBAA super-host detection benchmark on B300 (sm_103a).
+
+One step = one time window through the whole hot path: zero the cube,
+Alg. 1 over every packet of the window (already resident in HBM), then the
+end-of-window pass (zero counts, eps/Zmax, Alg. 2 hot columns, Alg. 3 tuple
+join + union checks, Thm. 2 estimates, sort).  The metric is packets per
+second of that step (Gpps); detect latency and the update kernel's share of
+its roofs are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cbaa|reference]
+                    [--workload window64m|window1m]
+
+Under torchrun each rank runs its own window (weak scaling, no collective
+on the data path); the step time is the maximum over ranks.
+`--impl reference` times the plain CPU oracle on a bounded sample of the
+same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1901_06207_b300 import traffic as T  # noqa: E402
+
+METRIC = "packets/sec (Gpps) cube update + end-of-window detect ms; fraction of HBM/L2-atomic peak"
+
+
+def workload(name: str):
+    from paper_1901_06207_b300.cbaa import make_params
+    if name == "window64m":
+        geo = make_params(5, 3, 1, 10, [12])
+        spec = T.spec_window_64m()
+        desc = dict(workload="window_64m_l2_cube", packets_per_window=spec.n_packets, source_pool=spec.n_hosts,
+                    planted_super_hosts=spec.n_planted, planted_peers="log-uniform [1024, 200000]",
+                    background="Zipf(1.1) sources over the pool, uniform 2^32 peers", duplicate_fraction=0.3,
+                    theta=1024, geometry="r=5, |RA|=3, |VA|=1, g=2^10, c=2^12 (64 MiB cube)")
+    elif name == "window1m":
+        geo = make_params(4, 3, 1, 12, [12])
+        spec = T.spec_window_1m()
+        desc = dict(workload="window_1m_paper_cube", packets_per_window=spec.n_packets, sources=10_000,
+                    planted_super_hosts=20, theta=1024, geometry="r=4, |RA|=3, |VA|=1, g=2^12, c=2^12 (128 MiB)")
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return geo, spec, 1024, desc
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons of one GPU through NVML while running."""
+
+    NAMES = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+             0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+             0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+    def __init__(self, index: int, period_s: float = 0.005):
+        self.index, self.period = index, period_s
+        self.samples, self.reasons = [], 0
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._t = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+        except Exception as e:  # noqa: BLE001
+            self.nv, self.err = None, str(e)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
+                self.reasons |= self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+            except Exception:  # noqa: BLE001
+                pass
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.nv is not None:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join()
+
+    def summary(self):
+        if self.nv is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": getattr(self, "err", "nvml")}
+        names = [n for bit, n in self.NAMES.items() if self.reasons & bit]
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_over_ranks(x: float, world: int, op: str, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+
+def oracle_sample(geo, pairs: np.ndarray, theta: int, n_sample: int):
+    """Time the plain CPU oracle (single thread) on the first n_sample packets + one detect."""
+    from oracle import oracle as O
+    O.build()
+    sample = np.ascontiguousarray(pairs[:n_sample])
+    t0 = time.perf_counter()
+    cube = O.build_cube(geo, sample)
+    t1 = time.perf_counter()
+    res = O.detect(geo, cube, theta)
+    t2 = time.perf_counter()
+    return {"update_s": t1 - t0, "detect_s": t2 - t1, "packets": int(n_sample), "hosts": int(res["hosts"].size)}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(geo, pairs, theta, n_sample):
+    r = oracle_sample(geo, pairs, theta, n_sample)
+    v = r["packets"] / (r["update_s"] + r["detect_s"]) / 1e9
+    return {"value": v, "unit": "Gpps", "cores": 1, "kind": "oracle",
+            "sample": f"first {r['packets']} packets of the window (Alg. 1) + one full detect of that cube; "
+                      f"update {r['update_s']:.3f} s, detect {r['detect_s']:.3f} s, single-threaded C",
+            "cpu": _cpu_model(), "host_cores": os.cpu_count()}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    geo, spec, theta, desc = workload(args.workload)
+    w = T.make_window(spec)
+    n_sample = min(spec.n_packets, args.reference_sample)
+    for _ in range(args.warmup):
+        oracle_sample(geo, w.pairs, theta, n_sample)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(geo, w.pairs, theta, n_sample)
+    elapsed = time.perf_counter() - t_all
+    v = n_sample * args.steps / elapsed / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gpps", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": desc,
+            "cpu_baseline": {"value": v, "unit": "Gpps", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: first {n_sample} packets of the window + one full detect",
+                             "cpu": _cpu_model()},
+            "e2e": {"value": v, "unit": "Gpps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+def load_traffic(workload_name: str):
+    """DRAM bytes per update launch from the committed ncu summary, if it is current."""
+    p = os.path.join(ROOT, "profiles", f"k_update_{workload_name}.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("dram_bytes_per_launch")
+    return None
+
+
+def run_cbaa(args):
+    import torch
+    from paper_1901_06207_b300 import cbaa as C
+
+    rank, world, local = dist_env()
+    assert torch.cuda.is_available(), "the CBAA path runs on a CUDA device only"
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    geo, spec0, theta, desc = workload(args.workload)
+    spec = spec0 if rank == 0 else T.TrafficSpec(**{**spec0.__dict__, "seed": spec0.seed + 0x100 * rank})
+    w = T.make_window(spec)
+    n = w.pairs.shape[0]
+    pairs_dev = torch.from_numpy(w.pairs.view(np.int32)).to(dev)
+    pairs_pin = torch.from_numpy(w.pairs.view(np.int32)).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+
+    cube = C.Cube(geo, device=dev)
+    ws = C.Workspace(geo, max_candidates=1 << 18, device=dev)
+    cap = 1 << 16
+    out = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
+    info = torch.zeros(8, dtype=torch.int32, device=dev)
+    kernels_per_step = 1 + 3 + (geo["n_ra"] - 1) + 1   # update | zero counts, eps/zmax, hot lists, joins, sort
+
+    def step(ev=None):
+        cube.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        cube.update(pairs_dev)
+        if ev is not None:
+            ev[1].record(stream)
+        cube.detect_async(theta, ws, out, info)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    hosts, inf = C.hosts_from_device(out, info)
+    assert inf["status"] == C.OK, inf
+
+    # L2 RED.OR roof on a buffer the size of the cube (the update kernel's bound)
+    red_buf = torch.empty(cube.nbytes // 4, dtype=torch.int32, device=dev)
+    n_ops = 4 * n
+    red_rates = []
+    for rep in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = C.lib().cbaa_bench_red_or(red_buf.data_ptr(), red_buf.numel(), n_ops, rep, stream.cuda_stream)
+        e1.record(stream)
+        assert st == 0, st
+        torch.cuda.synchronize()
+        if rep:
+            red_rates.append(n_ops / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    red_peak = max(red_rates)
+    del red_buf
+
+    # timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    total_ms = t_start.elapsed_time(t_end)
+    total_ms_max = reduce_over_ranks(total_ms, world, "max", dev)
+    upd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    det_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    hosts, inf = C.hosts_from_device(out, info)
+    assert inf["status"] == C.OK, inf
+    packets_all = reduce_over_ranks(float(n), world, "sum", dev)
+    value = packets_all * args.steps / (total_ms_max * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: H2D of the window's
+    # packets from pinned memory, update, synchronous detect with the host list
+    # copied back.
+    e2e_steps = max(3, min(args.steps, 10))
+    d2h = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pairs_dev.copy_(pairs_pin, non_blocking=True)
+        cube.reset()
+        cube.update(pairs_dev)
+        h = cube.detect(theta, ws=ws, cap=cap)
+        d2h += h.nbytes + C.INFO_BYTES
+    torch.cuda.synchronize()
+    e2e_s = reduce_over_ranks(time.perf_counter() - t0, world, "max", dev)
+    e2e_value = packets_all * e2e_steps / e2e_s / 1e9
+
+    hbm_peak, hbm_src = measured_peaks()
+    upd_s = statistics.mean(upd_ms) * 1e-3
+    red_achieved = 4 * n / upd_s / 1e9
+    traffic = load_traffic(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {**desc, "l2": "inputs larger than L2: each step streams a 512 MiB packet buffer; "
+                                 "the 64 MiB cube is L2-resident by design and re-zeroed every step",
+                   "parallelism": "one window per rank" if world > 1 else "single GPU"},
+        "update_ms": statistics.mean(upd_ms), "update_gpps": n / upd_s / 1e9,
+        "detect_ms": statistics.mean(det_ms), "detect_ms_p50": statistics.median(det_ms),
+        "hosts_detected": int(inf["n_hosts"]), "hot_columns": int(inf["n_hot"]),
+        "roofline": {"bound": "l2_atomic", "kernel": "k_update (Alg. 1)", "achieved": red_achieved,
+                     "peak": red_peak, "unit": "Gop/s", "frac": red_achieved / red_peak,
+                     "peak_source": "RED.OR microbenchmark on a cube-sized buffer, measured in this run",
+                     "units_per_launch": f"{4 * n} single-bit reductions ({n} packets x 4 arrays)",
+                     "traffic": traffic},
+        "roofline_hbm": {"bound": "hbm", "kernel": "k_update (Alg. 1)", "achieved": 8 * n / upd_s / 1e9,
+                         "peak": hbm_peak, "unit": "GB/s", "frac": 8 * n / upd_s / 1e9 / hbm_peak,
+                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})",
+                         "traffic": traffic},
+        "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clocks.summary(),
+        "e2e": {"value": e2e_value, "unit": "Gpps", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": int(d2h / e2e_steps), "steps": e2e_steps,
+                "path": "pinned host packets -> H2D -> cbaa_cube_update -> cbaa_detect (host list)"},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(geo, w.pairs, theta, min(n, args.reference_sample))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["cbaa", "reference"], default="cbaa")
+    ap.add_argument("--workload", default="window64m", choices=["window64m", "window1m"])
+    ap.add_argument("--reference-sample", type=int, default=4 << 20,
+                    help="packets per CPU-oracle step (bounded sample of the window)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "cbaa":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    return run_reference(args) if args.impl == "reference" else run_cbaa(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
