@@ -179,6 +179,32 @@ int cbaa_detect_async(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_
 int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_bytes,
                 cbaa_host *host_out, size_t cap, size_t *n_out, void *stream);
 
+/* Largest detect scratch that cbaa_detect_static can use (bytes). */
+#define CBAA_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* Detect without any device allocation, async.  The paper has no
+ * counterpart: this exists for callers that cannot obtain device memory at
+ * run time -- for example code running inside a host application that owns
+ * all GPU memory through its own pool and forbids cudaMalloc, or a capture
+ * agent with a fixed memory budget that must not grow while traffic flows
+ * (cudaMalloc can also stall other work on the device or fail under memory
+ * pressure from co-located processes).  It computes exactly what
+ * cbaa_detect_async computes, but its scratch is a library-owned static
+ * device array of CBAA_STATIC_SCRATCH_BYTES that every device loading the
+ * library keeps until the process exits.  The caller still passes the
+ * output records (dev_out, room for cap) and dev_info.
+ *  - The first call on a device looks the array up on that device (make
+ *    that device current, and make this first call before any stream
+ *    capture).
+ *  - The call clears the scratch state it relies on, but all calls share
+ *    one array: calls that overlap on the GPU (other streams, other host
+ *    threads, the same device) race and give wrong results.
+ *  - A geometry whose fixed tables do not fit returns CBAA_ERR_WORKSPACE
+ *    before enqueuing anything; more candidate tuples than fit are reported
+ *    in dev_info (status CBAA_ERR_WORKSPACE), as with cbaa_detect_async. */
+int cbaa_detect_static(const cbaa_cube *cube, uint32_t theta, cbaa_host *dev_out, size_t cap,
+                       cbaa_detect_info *dev_info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

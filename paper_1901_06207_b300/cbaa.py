@@ -75,6 +75,7 @@ def _signatures():
         "cbaa_detect_async": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, sz, vp, vp]),
         "cbaa_detect": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, sz, ctypes.POINTER(sz), vp]),
         "cbaa_bench_red_or": (ctypes.c_int, [vp, sz, sz, ctypes.c_uint32, vp]),
+        "cbaa_detect_static": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, vp]),
     }
 
 
