@@ -67,7 +67,9 @@ def measured_peaks():
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """Samples SM clock and clock-event reasons of one GPU through NVML while running."""
+    """Samples SM clock and clock-event reasons of one GPU while running.
+
+    Uses NVML through pynvml when it imports, else polls nvidia-smi."""
 
     NAMES = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
              0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
@@ -78,15 +80,16 @@ class ClockSampler:
         self.samples, self.reasons = [], 0
         self.max_mhz = None
         self._stop = threading.Event()
-        self._t = None
+        self._t = self._proc = None
+        self.source = "nvml"
         try:
             import pynvml
             pynvml.nvmlInit()
             self.nv = pynvml
             self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-        except Exception as e:  # noqa: BLE001
-            self.nv, self.err = None, str(e)
+        except Exception:  # noqa: BLE001
+            self.nv, self.source = None, "nvidia-smi"
 
     def _run(self):
         while not self._stop.is_set():
@@ -101,19 +104,41 @@ class ClockSampler:
         if self.nv is not None:
             self._t = threading.Thread(target=self._run, daemon=True)
             self._t.start()
+        else:
+            import subprocess
+            try:
+                self._proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.index),
+                     "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                     "--format=csv,noheader,nounits", "-lms", "20"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except OSError:
+                self._proc = None
         return self
 
     def __exit__(self, *a):
         self._stop.set()
         if self._t:
             self._t.join()
+        if self._proc is not None:
+            time.sleep(0.05)
+            self._proc.terminate()
+            out, _ = self._proc.communicate(timeout=10)
+            for line in out.splitlines():
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 3:
+                    continue
+                try:
+                    self.samples.append(float(parts[0]))
+                    self.max_mhz = float(parts[1])
+                    self.reasons |= int(parts[2], 16)
+                except ValueError:
+                    pass
 
     def summary(self):
-        if self.nv is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": getattr(self, "err", "nvml")}
         names = [n for bit, n in self.NAMES.items() if self.reasons & bit]
         return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
-                "reasons": names, "samples": len(self.samples)}
+                "reasons": names, "samples": len(self.samples), "source": self.source}
 
 
 # ----------------------------------------------------------------------------- distributed plumbing
@@ -211,9 +236,9 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU leg
 
-def load_traffic(workload_name: str):
-    """DRAM bytes per update launch from the committed ncu summary, if it is current."""
-    p = os.path.join(ROOT, "profiles", f"k_update_{workload_name}.json")
+def load_traffic(workload_name: str, path: str):
+    """DRAM bytes of one window's update from the committed ncu summary, if it is current."""
+    p = os.path.join(ROOT, "profiles", f"update_{path}_{workload_name}.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
@@ -240,16 +265,25 @@ def run_cbaa(args):
 
     cube = C.Cube(geo, device=dev)
     ws = C.Workspace(geo, max_candidates=1 << 18, device=dev)
+    uws = C.UpdateWorkspace(geo, n, device=dev) if args.update == "binned" else None
     cap = 1 << 16
     out = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
     info = torch.zeros(8, dtype=torch.int32, device=dev)
-    kernels_per_step = 1 + 3 + (geo["n_ra"] - 1) + 1   # update | zero counts, eps/zmax, hot lists, joins, sort
+    # update (direct: 1 kernel; binned: count, scan, scatter, apply) | detect: zero counts, eps/zmax,
+    # hot lists, |RA|-1 joins, sort
+    kernels_per_step = (4 if uws is not None else 1) + 3 + (geo["n_ra"] - 1) + 1
+
+    def do_update():
+        if uws is not None:
+            cube.update_binned(pairs_dev, uws)
+        else:
+            cube.update(pairs_dev)
 
     def step(ev=None):
         cube.reset()
         if ev is not None:
             ev[0].record(stream)
-        cube.update(pairs_dev)
+        do_update()
         if ev is not None:
             ev[1].record(stream)
         cube.detect_async(theta, ws, out, info)
@@ -277,6 +311,18 @@ def run_cbaa(args):
             red_rates.append(n_ops / (e0.elapsed_time(e1) * 1e-3) / 1e9)
     red_peak = max(red_rates)
     del red_buf
+
+    # the direct RED.OR update on the same window, for comparison with the chosen path
+    direct_ms = []
+    for rep in range(4):
+        cube.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cube.update(pairs_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            direct_ms.append(e0.elapsed_time(e1))
 
     # timed region
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
@@ -310,7 +356,7 @@ def run_cbaa(args):
     for _ in range(e2e_steps):
         pairs_dev.copy_(pairs_pin, non_blocking=True)
         cube.reset()
-        cube.update(pairs_dev)
+        do_update()
         h = cube.detect(theta, ws=ws, cap=cap)
         d2h += h.nbytes + C.INFO_BYTES
     torch.cuda.synchronize()
@@ -319,8 +365,7 @@ def run_cbaa(args):
 
     hbm_peak, hbm_src = measured_peaks()
     upd_s = statistics.mean(upd_ms) * 1e-3
-    red_achieved = 4 * n / upd_s / 1e9
-    traffic = load_traffic(args.workload)
+    traffic = load_traffic(args.workload, args.update)
     line = {
         "metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -331,15 +376,20 @@ def run_cbaa(args):
         "update_ms": statistics.mean(upd_ms), "update_gpps": n / upd_s / 1e9,
         "detect_ms": statistics.mean(det_ms), "detect_ms_p50": statistics.median(det_ms),
         "hosts_detected": int(inf["n_hosts"]), "hot_columns": int(inf["n_hot"]),
-        "roofline": {"bound": "l2_atomic", "kernel": "k_update (Alg. 1)", "achieved": red_achieved,
-                     "peak": red_peak, "unit": "Gop/s", "frac": red_achieved / red_peak,
-                     "peak_source": "RED.OR microbenchmark on a cube-sized buffer, measured in this run",
-                     "units_per_launch": f"{4 * n} single-bit reductions ({n} packets x 4 arrays)",
+        "update_path": args.update,
+        "roofline": {"bound": "hbm", "kernel": f"update ({args.update}: " +
+                     ("count+scan+scatter+apply" if uws is not None else "k_update") + ")",
+                     "achieved": 8 * n / upd_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": 8 * n / upd_s / 1e9 / hbm_peak,
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})",
+                     "units_per_launch": f"{n} packets x 8 B (the packet stream Alg. 1 must read)",
                      "traffic": traffic},
-        "roofline_hbm": {"bound": "hbm", "kernel": "k_update (Alg. 1)", "achieved": 8 * n / upd_s / 1e9,
-                         "peak": hbm_peak, "unit": "GB/s", "frac": 8 * n / upd_s / 1e9 / hbm_peak,
-                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})",
-                         "traffic": traffic},
+        "roofline_l2_atomic": {"bound": "l2_atomic", "kernel": "k_update (direct RED.OR design)",
+                               "achieved": 4 * n / (statistics.mean(direct_ms) * 1e-3) / 1e9, "peak": red_peak,
+                               "unit": "Gop/s",
+                               "frac": 4 * n / (statistics.mean(direct_ms) * 1e-3) / 1e9 / red_peak,
+                               "peak_source": "RED.OR microbenchmark on a cube-sized buffer, measured in this run",
+                               "update_ms": statistics.mean(direct_ms)},
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_value, "unit": "Gpps", "h2d_bytes_per_step": 8 * n,
@@ -359,10 +409,12 @@ def run_cbaa(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cbaa", "reference"], default="cbaa")
     ap.add_argument("--workload", default="window64m", choices=["window64m", "window1m"])
+    ap.add_argument("--update", default="binned", choices=["binned", "direct"],
+                    help="Alg. 1 path: partitioned by cube tile (binned) or RED.OR into the cube (direct)")
     ap.add_argument("--reference-sample", type=int, default=4 << 20,
                     help="packets per CPU-oracle step (bounded sample of the window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -145,6 +145,22 @@ int cbaa_cube_reset(cbaa_cube *cube, void *stream);
  * n = 0 is a no-op. */
 int cbaa_cube_update(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *stream);
 
+/* Bytes of workspace that cbaa_cube_update_binned needs to route up to
+ * max_pairs packets per pass (0 if p is invalid or its cube exceeds the
+ * binned path's limit of 512 MiB).  Host only. */
+size_t cbaa_update_workspace_bytes(const cbaa_params *p, size_t max_pairs);
+
+/* Alg. 1 (Section III.B), async, partitioned: the same cube bits as
+ * cbaa_cube_update, set without L2 atomics on hot columns.  Each bit set is
+ * routed to the 128 KiB cube tile holding its word; tiles are assembled in
+ * shared memory and ORed into the cube.  dev_ws: ws_bytes of caller device
+ * memory (16-byte aligned), from cbaa_update_workspace_bytes; a workspace
+ * sized for fewer than n packets is used in several passes.  Returns
+ * CBAA_ERR_INVALID_ARG for cubes above 512 MiB or a workspace too small for
+ * one packet. */
+int cbaa_cube_update_binned(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *dev_ws, size_t ws_bytes,
+                            void *stream);
+
 /* Section III.C merge, async: dst |= src_0 | ... | src_{k-1} word by word.
  * All cubes must share dst's geometry (else CBAA_ERR_GEOMETRY); k = 0 is a
  * no-op; dst may not be among srcs. */

@@ -76,6 +76,8 @@ def _signatures():
         "cbaa_detect": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, sz, ctypes.POINTER(sz), vp]),
         "cbaa_bench_red_or": (ctypes.c_int, [vp, sz, sz, ctypes.c_uint32, vp]),
         "cbaa_detect_static": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, vp]),
+        "cbaa_update_workspace_bytes": (sz, [P, sz]),
+        "cbaa_cube_update_binned": (ctypes.c_int, [vp, vp, sz, vp, sz, vp]),
     }
 
 
@@ -180,6 +182,26 @@ class Workspace:
         return self.buf.data_ptr()
 
 
+def update_workspace_bytes(d: dict, max_pairs: int) -> int:
+    return int(lib().cbaa_update_workspace_bytes(ctypes.byref(params(d)), max_pairs))
+
+
+class UpdateWorkspace:
+    """Workspace of the partitioned update, sized for ``max_pairs`` packets per pass."""
+
+    def __init__(self, d: dict, max_pairs: int, device="cuda"):
+        torch = _torch()
+        self.nbytes = update_workspace_bytes(d, max_pairs)
+        if self.nbytes == 0:
+            raise CbaaError(ERR_INVALID_ARG, "update workspace size")
+        self.max_pairs = max_pairs
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+
+    @property
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+
 class Cube:
     """A cube of bit arrays in caller (torch) device memory."""
 
@@ -220,6 +242,16 @@ class Cube:
 
     def update_ptr(self, ptr: int, n: int, stream=None):
         _check(lib().cbaa_cube_update(self.handle, ptr, n, _stream_ptr(stream)), "cube_update")
+
+    def update_binned(self, pairs, ws: "UpdateWorkspace", n: int | None = None, stream=None):
+        """Partitioned Alg. 1 (same bits as update) using an UpdateWorkspace."""
+        if n is None:
+            n = pairs.shape[0] if pairs.dim() == 2 else pairs.numel() // 2
+        self.update_binned_ptr(pairs.data_ptr(), n, ws, stream)
+
+    def update_binned_ptr(self, ptr: int, n: int, ws: "UpdateWorkspace", stream=None):
+        _check(lib().cbaa_cube_update_binned(self.handle, ptr, n, ws.ptr, ws.nbytes, _stream_ptr(stream)),
+               "cube_update_binned")
 
     def merge(self, others, stream=None):
         arr = (ctypes.c_void_p * max(1, len(others)))(*[o.handle.value for o in others])

@@ -6,6 +6,7 @@
 
 #include "cbaa_internal.cuh"
 #include "detect_layout.h"
+#include "update_binned.h"
 
 struct cbaa_cube {
     cbaa_params p;
@@ -162,6 +163,27 @@ int cbaa_cube_update(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void 
     if (!dev_pairs || (reinterpret_cast<uintptr_t>(dev_pairs) & 7u)) return CBAA_ERR_INVALID_ARG;
     return cbaa::launch_update(cube->G, cube->data, dev_pairs, n, as_stream(stream)) == cudaSuccess ? CBAA_OK
                                                                                                     : CBAA_ERR_CUDA;
+}
+
+size_t cbaa_update_workspace_bytes(const cbaa_params *p, size_t max_pairs) {
+    if (validate(p) != CBAA_OK || max_pairs == 0) return 0;
+    const Geo G = cbaa::make_geo(*p);
+    if (cbaa::bin_count(G) > cbaa::kMaxBins) return 0;
+    return cbaa::bin_ws_bytes(G, max_pairs);
+}
+
+int cbaa_cube_update_binned(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *dev_ws, size_t ws_bytes,
+                            void *stream) {
+    if (!cube) return CBAA_ERR_INVALID_ARG;
+    if (n == 0) return CBAA_OK;
+    if (!dev_pairs || (reinterpret_cast<uintptr_t>(dev_pairs) & 7u)) return CBAA_ERR_INVALID_ARG;
+    if (!dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u)) return CBAA_ERR_INVALID_ARG;
+    if (cbaa::bin_count(cube->G) > cbaa::kMaxBins) return CBAA_ERR_INVALID_ARG;
+    cbaa::BinWs W;
+    if (!cbaa::bin_ws_make(cube->G, dev_ws, ws_bytes, &W)) return CBAA_ERR_INVALID_ARG;
+    return cbaa::launch_update_binned(cube->G, cube->data, dev_pairs, n, W, as_stream(stream)) == cudaSuccess
+               ? CBAA_OK
+               : CBAA_ERR_CUDA;
 }
 
 int cbaa_cube_merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream) {

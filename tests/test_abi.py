@@ -99,3 +99,12 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(cbaa, "_lib", None)
     with pytest.raises(ImportError):
         cbaa.lib()
+
+
+def test_update_workspace_limits(C):
+    """The partitioned update covers cubes up to 512 MiB; larger ones get no workspace size."""
+    assert C.update_workspace_bytes(GEO.L2, 1 << 20) >= (1 << 20) * 4 * 4
+    assert C.update_workspace_bytes(GEO.SERVE, 1) > 0
+    big = C.make_params(8, 3, 1, 10, [13])          # 1 GiB cube
+    assert C.validate(big) == C.OK and C.update_workspace_bytes(big, 1024) == 0
+    assert C.update_workspace_bytes(GEO.L2, 0) == 0

@@ -77,6 +77,34 @@ def test_update_cube_bit_exact(C, oracle, geo, win):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("geo,win", CUBE_CASES)
+def test_binned_update_cube_bit_exact(C, oracle, geo, win):
+    """The partitioned update sets exactly the bits of Alg. 1."""
+    d = GEO.ALL[geo]
+    w = window(win)
+    cube = C.Cube(d)
+    ws = C.UpdateWorkspace(d, w.pairs.shape[0])
+    cube.update_binned(dev_pairs(w.pairs), ws)
+    assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
+
+
+def test_binned_update_passes_ragged_and_incremental(C, oracle):
+    """Small workspace (many passes), odd counts, 8-byte-aligned starts, on top of earlier bits."""
+    import torch
+    d = GEO.L2
+    w = window("4m")
+    p = dev_pairs(w.pairs)
+    cube = C.Cube(d)
+    half = 1_000_001
+    cube.update(p, n=half)                                  # earlier bits from the direct path
+    ws = C.UpdateWorkspace(d, 300_007)
+    bounds = [half, half + 1, half + 8191, 2_500_003, w.pairs.shape[0]]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        cube.update_binned_ptr(p.data_ptr() + 8 * a, b - a, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
+
+
 def test_update_ragged_and_unaligned(C, oracle):
     """Odd counts, a start that is only 8-byte aligned, empty and one-pair calls, uneven batches."""
     import torch
