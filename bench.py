@@ -265,7 +265,10 @@ def run_cbaa(args):
 
     cube = C.Cube(geo, device=dev)
     ws = C.Workspace(geo, max_candidates=1 << 18, device=dev)
-    uws = C.UpdateWorkspace(geo, n, device=dev) if args.update == "binned" else None
+    from paper_1901_06207_b300 import autotune
+    tuned = autotune.tune_update(geo, pairs_dev, device=dev, use_cache=False)
+    path = tuned["path"] if args.update == "auto" else args.update
+    uws = C.UpdateWorkspace(geo, n, device=dev) if path == "binned" else None
     cap = 1 << 16
     out = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
     info = torch.zeros(8, dtype=torch.int32, device=dev)
@@ -365,7 +368,7 @@ def run_cbaa(args):
 
     hbm_peak, hbm_src = measured_peaks()
     upd_s = statistics.mean(upd_ms) * 1e-3
-    traffic = load_traffic(args.workload, args.update)
+    traffic = load_traffic(args.workload, path)
     line = {
         "metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -376,8 +379,10 @@ def run_cbaa(args):
         "update_ms": statistics.mean(upd_ms), "update_gpps": n / upd_s / 1e9,
         "detect_ms": statistics.mean(det_ms), "detect_ms_p50": statistics.median(det_ms),
         "hosts_detected": int(inf["n_hosts"]), "hot_columns": int(inf["n_hot"]),
-        "update_path": args.update,
-        "roofline": {"bound": "hbm", "kernel": f"update ({args.update}: " +
+        "update_path": path,
+        "autotune": {"pick": tuned["path"], "tuning": tuned["tuning"], "best_ms": tuned["ms"],
+                     "worst_ms": tuned["worst_ms"], "candidates": tuned["candidates"]},
+        "roofline": {"bound": "hbm", "kernel": f"update ({path}: " +
                      ("count+scan+scatter+apply" if uws is not None else "k_update") + ")",
                      "achieved": 8 * n / upd_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": 8 * n / upd_s / 1e9 / hbm_peak,
@@ -406,22 +411,131 @@ def run_cbaa(args):
     return 0
 
 
+def _router_window_job(args):
+    seed, n_routers = args
+    spec = T.spec_window_64m(seed=seed, scale_shift=2)
+    pairs, counts, _ = T.router_window(spec, n_routers)
+    return pairs, counts
+
+
+def make_router_windows(n_windows: int, n_routers: int, seed0: int = 0xC0FFEE20):
+    """16M-packet windows (the 64M window's shape scaled by 1/4) split over routers, in a spawn pool."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(n_windows, max(1, (os.cpu_count() or 2) // 2))) as pool:
+        return pool.map(_router_window_job, [(seed0 + w, n_routers) for w in range(n_windows)])
+
+
+def run_batched(args):
+    """Batched router windows: one CUDA graph replays every window (update pass over all router cubes,
+    OR-merge, detect); the plain single-cube path on the same windows is timed beside it."""
+    rank, world, local = dist_env()
+    wins = make_router_windows(args.windows, args.routers, 0xC0FFEE20 + 0x1000 * rank)   # before CUDA init
+    import torch
+    from paper_1901_06207_b300 import cbaa as C
+    from paper_1901_06207_b300.batch import RouterWindows
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    geo = C.make_params(5, 3, 1, 10, [12])
+    theta, R = 1024, args.routers
+    n_per = [int(c.sum()) for _, c in wins]
+    dev_w, flat = [], []
+    for pairs, counts in wins:
+        p = torch.from_numpy(pairs.view(np.int32)).to(dev)
+        flat.append(p)
+        b = np.concatenate([[0], np.cumsum(counts)])
+        dev_w.append([p[b[j]:b[j + 1]] if counts[j] else None for j in range(R)])
+    rw = RouterWindows(geo, R, theta, max_pairs=max(n_per), n_windows=len(wins), device=dev)
+    rw.capture(dev_w)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):
+        rw.replay()
+    torch.cuda.synchronize()
+    res = rw.results()
+    assert all(inf["status"] == C.OK for _, inf in res), [inf for _, inf in res]
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return reduce_over_ranks(e0.elapsed_time(e1), world, "max", dev)
+
+    steps = max(1, args.steps)
+    with ClockSampler(local) as clocks:
+        ms = timed(rw.replay, steps)
+    total_packets = reduce_over_ranks(float(sum(n_per)), world, "sum", dev)
+    value = total_packets * steps / (ms * 1e-3) / 1e9
+
+    # the plain single-cube path on the same windows: one cube, partitioned update of the whole
+    # window, detect; eager launches, no routers, no graph
+    cube = C.Cube(geo, device=dev)
+    ws = C.Workspace(geo, device=dev)
+    uws = C.UpdateWorkspace(geo, max(n_per), device=dev)
+    out = torch.zeros(4 * rw.cap, dtype=torch.int32, device=dev)
+    info = torch.zeros(8, dtype=torch.int32, device=dev)
+
+    def plain():
+        for p in flat:
+            cube.reset()
+            cube.update_binned(p, uws)
+            cube.detect_async(theta, ws, out, info)
+
+    plain()
+    plain_ms = timed(plain, steps)
+    hosts_last, _ = C.hosts_from_device(out, info)
+    assert np.array_equal(hosts_last, res[-1][0]), "plain and batched host lists differ"
+    plain_value = total_packets * steps / (plain_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batched_{len(wins)}x16m_{R}_routers",
+                       "windows": len(wins), "routers": R, "packets_per_window": n_per[0],
+                       "router_loads": "lognormal(sigma=0.8) weights over a 5-tuple hash",
+                       "geometry": "r=5, |RA|=3, |VA|=1, g=2^10, c=2^12 (64 MiB per cube)", "theta": theta,
+                       "step": "one CUDA graph replay: per window reset router cubes, one partitioned update "
+                               "pass over all routers, OR-merge, detect",
+                       "l2": "inputs larger than L2 (2 GiB of packets per step)"},
+            "window_ms": ms / steps / len(wins),
+            "plain_single_cube": {"value": plain_value, "unit": "Gpps", "window_ms": plain_ms / steps / len(wins),
+                                  "path": "one cube, partitioned update of the whole window, detect, no graph"},
+            "hosts_per_window": [int(i["n_hosts"]) for _, i in res],
+            "gpu_launches": steps * len(wins) * (4 + 1 + 3 + (geo["n_ra"] - 1) + 1),
+            "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cbaa", "reference"], default="cbaa")
-    ap.add_argument("--workload", default="window64m", choices=["window64m", "window1m"])
-    ap.add_argument("--update", default="binned", choices=["binned", "direct"],
-                    help="Alg. 1 path: partitioned by cube tile (binned) or RED.OR into the cube (direct)")
+    ap.add_argument("--workload", default="window64m", choices=["window64m", "window1m", "batched"])
+    ap.add_argument("--update", default="auto", choices=["auto", "binned", "direct"],
+                    help="Alg. 1 path: partitioned by cube tile (binned), RED.OR into the cube (direct), "
+                         "or the autotuner's pick (auto)")
+    ap.add_argument("--windows", type=int, default=16, help="batched workload: windows per batch")
+    ap.add_argument("--routers", type=int, default=8, help="batched workload: simulated edge routers")
     ap.add_argument("--reference-sample", type=int, default=4 << 20,
                     help="packets per CPU-oracle step (bounded sample of the window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "cbaa":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    return run_reference(args) if args.impl == "reference" else run_cbaa(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_batched(args) if args.workload == "batched" else run_cbaa(args)
 
 
 if __name__ == "__main__":

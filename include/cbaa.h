@@ -107,10 +107,24 @@ typedef struct cbaa_detect_info {
     uint32_t reserved[3];
 } cbaa_detect_info;
 
+/* Launch shapes of the update kernels (process-wide; see cbaa_set_tuning).
+ * Zero fields take the defaults. */
+typedef struct cbaa_tuning {
+    uint32_t scatter_shape;        /* partitioned update, routing kernel: 0 = 512 threads x 8 packets,
+                                      1 = 512 x 4, 2 = 1024 x 4, 3 = 256 x 8, 4 = 256 x 4 */
+    uint32_t count_blocks_per_sm;  /* partitioned update, counting kernel grid (default 8) */
+    uint32_t apply_items_per_sm;   /* partitioned update, tile-assembly items per SM (default 8) */
+    uint32_t direct_blocks_per_sm; /* direct update grid (default 8 blocks of 256 threads) */
+} cbaa_tuning;
+
 typedef struct cbaa_cube cbaa_cube;   /* opaque handle: a params copy plus the caller's memory */
 
 /* Human-readable name of a status code.  Never returns NULL. */
 const char *cbaa_status_str(int status);
+
+/* Name of the last CUDA runtime error behind a CBAA_ERR_CUDA returned to
+ * this host thread ("cudaSuccess" if none).  Never returns NULL. */
+const char *cbaa_last_cuda_error(void);
 
 /* Check a geometry against the rules above.  Host only, no device needed. */
 int cbaa_params_validate(const cbaa_params *p);
@@ -160,6 +174,25 @@ size_t cbaa_update_workspace_bytes(const cbaa_params *p, size_t max_pairs);
  * one packet. */
 int cbaa_cube_update_binned(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *dev_ws, size_t ws_bytes,
                             void *stream);
+
+/* Workspace for cbaa_cube_update_multi with n_cubes cubes of geometry p
+ * and up to max_pairs packets per pass (0 if invalid, n_cubes > 16, or the
+ * cubes together exceed 512 MiB).  Host only. */
+size_t cbaa_update_multi_workspace_bytes(const cbaa_params *p, int n_cubes, size_t max_pairs);
+
+/* Alg. 1 for several local cubes at once (the edge routers of Section
+ * III.C), async: packets dev_pairs[j][0..n[j]) go to cubes[j].  One
+ * partitioned pass covers all cubes, so uneven router loads share the whole
+ * GPU.  All cubes must have the same geometry (else CBAA_ERR_GEOMETRY);
+ * 1 <= n_cubes <= 16, together at most 512 MiB. */
+int cbaa_cube_update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs, const size_t *n,
+                           void *dev_ws, size_t ws_bytes, void *stream);
+
+/* Set / read the process-wide launch shapes of the update kernels (for an
+ * autotuner).  Results never depend on them.  Not synchronised with calls
+ * running on other host threads: set them before launching work. */
+int cbaa_set_tuning(const cbaa_tuning *t);
+int cbaa_get_tuning(cbaa_tuning *t);
 
 /* Section III.C merge, async: dst |= src_0 | ... | src_{k-1} word by word.
  * All cubes must share dst's geometry (else CBAA_ERR_GEOMETRY); k = 0 is a

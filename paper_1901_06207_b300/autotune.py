@@ -1,0 +1,88 @@
+"""Autotuner for the update path and its launch shapes.
+
+Times the direct update (grid sizes) and the partitioned update (routing
+shape x tile-assembly items x counting grid) on the caller's packets with
+CUDA events, keeps the fastest, sets it process-wide with cbaa_set_tuning
+and caches the choice per (GPU, geometry, packet-count bucket) in a JSON
+file.  Launch shapes never change results, only time.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import statistics
+
+from . import cbaa as C
+
+CACHE = os.path.join(os.path.expanduser("~"), ".cache", "cbaa", "tuning.json")
+
+
+def _key(geo: dict, n: int, device_name: str) -> str:
+    g = f"r{geo['r']}-ra{geo['n_ra']}-va{geo['n_va']}-g{geo['log2_g']}-c" + ".".join(
+        str(c) for c in geo["cbn"][:geo["n_ra"] + geo["n_va"]])
+    return f"{device_name}|{g}|n2^{max(0, int(n).bit_length() - 1)}"
+
+
+def candidates():
+    for b in (4, 8, 16, 32):
+        yield "direct", dict(direct_blocks_per_sm=b)
+    for shape, items, cnt in itertools.product(range(5), (4, 8, 16), (4, 8)):
+        yield "binned", dict(scatter_shape=shape, apply_items_per_sm=items, count_blocks_per_sm=cnt)
+
+
+def time_update(cube, pairs, path: str, ws, reps: int = 3) -> float:
+    torch = C._torch()
+    stream = torch.cuda.current_stream()
+    times = []
+    for rep in range(reps + 1):
+        cube.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if path == "binned":
+            cube.update_binned(pairs, ws)
+        else:
+            cube.update(pairs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def tune_update(geo: dict, pairs, device="cuda", reps: int = 3, use_cache: bool = True, cache_path: str = CACHE):
+    """Pick the fastest update path and shape for ``pairs`` (device [n, 2]); returns the record."""
+    torch = C._torch()
+    n = pairs.shape[0]
+    name = torch.cuda.get_device_name(device)
+    key = _key(geo, n, name)
+    cache = {}
+    if use_cache and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        rec = cache[key]
+        C.set_tuning(**rec["tuning"])
+        return {**rec, "cached": True}
+    cube = C.Cube(geo, device=device)
+    ws = C.UpdateWorkspace(geo, n, device=device)
+    results = []
+    for path, t in candidates():
+        C.set_tuning(**t)
+        results.append({"path": path, "tuning": C.get_tuning(), "ms": time_update(cube, pairs, path, ws, reps)})
+    best = min(results, key=lambda r: r["ms"])
+    C.set_tuning(**best["tuning"])
+    rec = {"path": best["path"], "tuning": best["tuning"], "ms": best["ms"], "candidates": len(results),
+           "worst_ms": max(r["ms"] for r in results), "key": key}
+    if use_cache:
+        cache[key] = rec
+        try:
+            os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError:
+            pass
+    return {**rec, "cached": False, "results": results}

@@ -1,0 +1,71 @@
+"""Batched windows over simulated edge routers, replayed as one CUDA graph.
+
+Section III.C's deployment: every edge router scans its own packets into a
+local cube (Alg. 1); at the end of each time window the global server ORs
+the local cubes together and restores the super hosts (Alg. 2, Alg. 3).
+Here the routers are local cubes on one GPU.  For each window the
+library's partitioned update feeds all router cubes in one pass (so uneven
+router loads share the whole GPU), the router cubes are OR-merged into the
+global cube, and the detect writes that window's host list to device
+memory.  A sequence of windows is recorded once into a CUDA graph and
+replayed with a single launch.
+
+Orchestration only: every step runs in libcbaa's kernels.
+"""
+from __future__ import annotations
+
+from . import cbaa as C
+
+
+class RouterWindows:
+    """Device state for ``n_windows`` windows of ``n_routers`` router cubes plus a global cube."""
+
+    def __init__(self, geo: dict, n_routers: int, theta: int, max_pairs: int, n_windows: int, cap: int = 1 << 14,
+                 max_candidates: int = 1 << 18, device="cuda"):
+        torch = C._torch()
+        self.geo, self.theta, self.cap = dict(geo), theta, cap
+        self.routers = [C.Cube(geo, device=device) for _ in range(n_routers)]
+        self.glob = C.Cube(geo, device=device)
+        self.uws = C.UpdateWorkspace(geo, max_pairs, device=device, n_cubes=n_routers)
+        self.dws = C.Workspace(geo, max_candidates=max_candidates, device=device)
+        self.out = torch.zeros((n_windows, 4 * cap), dtype=torch.int32, device=device)
+        self.info = torch.zeros((n_windows, 8), dtype=torch.int32, device=device)
+        self.graph = None
+        self._keep = None
+
+    def enqueue_window(self, w: int, router_pairs, stream=None):
+        """One window: reset router cubes, one update pass over all of them, merge, detect."""
+        for c in self.routers:
+            c.reset(stream)
+        C.update_multi(self.routers, router_pairs, self.uws, stream=stream)
+        self.glob.reset(stream)
+        self.glob.merge(self.routers, stream)
+        self.glob.detect_async(self.theta, self.dws, self.out[w], self.info[w], stream)
+
+    def enqueue(self, windows, stream=None):
+        for w, rp in enumerate(windows):
+            self.enqueue_window(w, rp, stream)
+
+    def capture(self, windows):
+        """Record every window into one CUDA graph (after one eager pass on a side stream)."""
+        torch = C._torch()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.enqueue(windows)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.enqueue(windows)
+        self.graph, self._keep = g, windows
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def results(self):
+        """[(hosts, info)] per window (synchronises)."""
+        torch = C._torch()
+        torch.cuda.synchronize()
+        return [C.hosts_from_device(self.out[w], self.info[w]) for w in range(self.out.shape[0])]

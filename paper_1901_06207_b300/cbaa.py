@@ -43,6 +43,11 @@ class DetectInfo(ctypes.Structure):
                 ("reserved", ctypes.c_uint32 * 3)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("scatter_shape", ctypes.c_uint32), ("count_blocks_per_sm", ctypes.c_uint32),
+                ("apply_items_per_sm", ctypes.c_uint32), ("direct_blocks_per_sm", ctypes.c_uint32)]
+
+
 HOST_DTYPE = np.dtype([("ip", "<u4"), ("z", "<u4"), ("est", "<f4"), ("flags", "<u4")])
 assert HOST_DTYPE.itemsize == ctypes.sizeof(Host) == 16
 INFO_BYTES = ctypes.sizeof(DetectInfo)
@@ -50,7 +55,8 @@ INFO_BYTES = ctypes.sizeof(DetectInfo)
 
 class CbaaError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__(f"{what}: {status_str(status)} ({status})")
+        extra = f" [{lib().cbaa_last_cuda_error().decode()}]" if status == ERR_CUDA else ""
+        super().__init__(f"{what}: {status_str(status)} ({status}){extra}")
         self.status = status
 
 
@@ -61,6 +67,7 @@ def _signatures():
     P, vp, sz = ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_size_t
     return {
         "cbaa_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+        "cbaa_last_cuda_error": (ctypes.c_char_p, []),
         "cbaa_params_validate": (ctypes.c_int, [P]),
         "cbaa_cube_bytes": (sz, [P]),
         "cbaa_detect_workspace_bytes": (sz, [P, sz]),
@@ -78,6 +85,11 @@ def _signatures():
         "cbaa_detect_static": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, vp]),
         "cbaa_update_workspace_bytes": (sz, [P, sz]),
         "cbaa_cube_update_binned": (ctypes.c_int, [vp, vp, sz, vp, sz, vp]),
+        "cbaa_update_multi_workspace_bytes": (sz, [P, ctypes.c_int, sz]),
+        "cbaa_cube_update_multi": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                                  ctypes.POINTER(sz), vp, sz, vp]),
+        "cbaa_set_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
+        "cbaa_get_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
     }
 
 
@@ -186,12 +198,38 @@ def update_workspace_bytes(d: dict, max_pairs: int) -> int:
     return int(lib().cbaa_update_workspace_bytes(ctypes.byref(params(d)), max_pairs))
 
 
-class UpdateWorkspace:
-    """Workspace of the partitioned update, sized for ``max_pairs`` packets per pass."""
+def update_multi_workspace_bytes(d: dict, n_cubes: int, max_pairs: int) -> int:
+    return int(lib().cbaa_update_multi_workspace_bytes(ctypes.byref(params(d)), n_cubes, max_pairs))
 
-    def __init__(self, d: dict, max_pairs: int, device="cuda"):
+
+def set_tuning(scatter_shape=0, count_blocks_per_sm=0, apply_items_per_sm=0, direct_blocks_per_sm=0):
+    t = Tuning(scatter_shape, count_blocks_per_sm, apply_items_per_sm, direct_blocks_per_sm)
+    _check(lib().cbaa_set_tuning(ctypes.byref(t)), "set_tuning")
+
+
+def get_tuning() -> dict:
+    t = Tuning()
+    _check(lib().cbaa_get_tuning(ctypes.byref(t)), "get_tuning")
+    return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+
+def update_multi(cubes, pairs_list, ws: "UpdateWorkspace", counts=None, stream=None):
+    """Alg. 1 for several router cubes in one partitioned pass: pairs_list[j] feeds cubes[j]."""
+    k = len(cubes)
+    hs = (ctypes.c_void_p * k)(*[c.handle.value for c in cubes])
+    ps = (ctypes.c_void_p * k)(*[p.data_ptr() if p is not None and p.numel() else None for p in pairs_list])
+    if counts is None:
+        counts = [0 if p is None else (p.shape[0] if p.dim() == 2 else p.numel() // 2) for p in pairs_list]
+    ns = (ctypes.c_size_t * k)(*counts)
+    _check(lib().cbaa_cube_update_multi(hs, k, ps, ns, ws.ptr, ws.nbytes, _stream_ptr(stream)), "cube_update_multi")
+
+
+class UpdateWorkspace:
+    """Workspace of the partitioned update, sized for ``max_pairs`` packets per pass over ``n_cubes`` cubes."""
+
+    def __init__(self, d: dict, max_pairs: int, device="cuda", n_cubes: int = 1):
         torch = _torch()
-        self.nbytes = update_workspace_bytes(d, max_pairs)
+        self.nbytes = update_multi_workspace_bytes(d, n_cubes, max_pairs)
         if self.nbytes == 0:
             raise CbaaError(ERR_INVALID_ARG, "update workspace size")
         self.max_pairs = max_pairs

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "cbaa_internal.cuh"
@@ -87,6 +88,24 @@ int validate(const cbaa_params *p) {
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+thread_local cudaError_t t_last_cuda = cudaSuccess;
+
+// CBAA_OK for cudaSuccess, else CBAA_ERR_CUDA with the error remembered for
+// cbaa_last_cuda_error().
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CBAA_OK;
+    t_last_cuda = e;
+    return CBAA_ERR_CUDA;
+}
+
+cbaa_tuning g_tuning = {};
+std::mutex g_tuning_mu;
+
+cbaa_tuning current_tuning() {
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    return g_tuning;
+}
+
 }  // namespace
 
 extern "C" {
@@ -106,6 +125,8 @@ const char *cbaa_status_str(int status) {
 }
 
 int cbaa_params_validate(const cbaa_params *p) { return validate(p); }
+
+const char *cbaa_last_cuda_error(void) { return cudaGetErrorName(t_last_cuda); }
 
 size_t cbaa_cube_bytes(const cbaa_params *p) {
     if (validate(p) != CBAA_OK) return 0;
@@ -154,36 +175,88 @@ int cbaa_cube_params(const cbaa_cube *cube, cbaa_params *out) {
 
 int cbaa_cube_reset(cbaa_cube *cube, void *stream) {
     if (!cube) return CBAA_ERR_INVALID_ARG;
-    return cudaMemsetAsync(cube->data, 0, cube->bytes, as_stream(stream)) == cudaSuccess ? CBAA_OK : CBAA_ERR_CUDA;
+    return cuda_status(cudaMemsetAsync(cube->data, 0, cube->bytes, as_stream(stream)));
 }
 
 int cbaa_cube_update(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *stream) {
     if (!cube) return CBAA_ERR_INVALID_ARG;
     if (n == 0) return CBAA_OK;
     if (!dev_pairs || (reinterpret_cast<uintptr_t>(dev_pairs) & 7u)) return CBAA_ERR_INVALID_ARG;
-    return cbaa::launch_update(cube->G, cube->data, dev_pairs, n, as_stream(stream)) == cudaSuccess ? CBAA_OK
-                                                                                                    : CBAA_ERR_CUDA;
+    return cuda_status(cbaa::launch_update(cube->G, cube->data, dev_pairs, n, current_tuning().direct_blocks_per_sm,
+                               as_stream(stream)));
 }
 
 size_t cbaa_update_workspace_bytes(const cbaa_params *p, size_t max_pairs) {
-    if (validate(p) != CBAA_OK || max_pairs == 0) return 0;
+    return cbaa_update_multi_workspace_bytes(p, 1, max_pairs);
+}
+
+size_t cbaa_update_multi_workspace_bytes(const cbaa_params *p, int n_cubes, size_t max_pairs) {
+    if (validate(p) != CBAA_OK || max_pairs == 0 || n_cubes < 1 || n_cubes > (int)cbaa::kMaxRouters) return 0;
     const Geo G = cbaa::make_geo(*p);
-    if (cbaa::bin_count(G) > cbaa::kMaxBins) return 0;
-    return cbaa::bin_ws_bytes(G, max_pairs);
+    if ((uint64_t)n_cubes * cbaa::tiles_per_cube(G) > cbaa::kMaxBins) return 0;
+    return cbaa::bin_ws_bytes(G, (uint32_t)n_cubes, max_pairs);
+}
+
+int cbaa_cube_update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs, const size_t *n,
+                           void *dev_ws, size_t ws_bytes, void *stream) {
+    if (!cubes || !dev_pairs || !n || n_cubes < 1 || n_cubes > (int)cbaa::kMaxRouters) return CBAA_ERR_INVALID_ARG;
+    if (!dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u)) return CBAA_ERR_INVALID_ARG;
+    const cbaa_cube *c0 = cubes[0];
+    if (!c0) return CBAA_ERR_INVALID_ARG;
+    const Geo &G = c0->G;
+    const uint32_t tpc = cbaa::tiles_per_cube(G);
+    if ((uint64_t)n_cubes * tpc > cbaa::kMaxBins) return CBAA_ERR_INVALID_ARG;
+    cbaa::BinSegs S;
+    std::memset(&S, 0, sizeof S);
+    S.n_routers = (uint32_t)n_cubes;
+    S.tiles_per_seg = tpc;
+    S.seg_words = tpc << cbaa::kBinTileBits;
+    uint64_t total = 0;
+    for (int j = 0; j < n_cubes; ++j) {
+        const cbaa_cube *c = cubes[j];
+        if (!c) return CBAA_ERR_INVALID_ARG;
+        if (std::memcmp(&c->p, &c0->p, sizeof(cbaa_params)) != 0) return CBAA_ERR_GEOMETRY;
+        for (int i = 0; i < j; ++i)
+            if (cubes[i] == c) return CBAA_ERR_INVALID_ARG;
+        S.cube[j] = c->data;
+        if (n[j] == 0) continue;
+        if (!dev_pairs[j] || (reinterpret_cast<uintptr_t>(dev_pairs[j]) & 7u)) return CBAA_ERR_INVALID_ARG;
+        S.pairs[S.k] = dev_pairs[j];
+        S.start[S.k] = total;
+        S.router[S.k] = (uint32_t)j;
+        ++S.k;
+        total += n[j];
+    }
+    S.start[S.k] = total;
+    if (total == 0) return CBAA_OK;
+    cbaa::BinWs W;
+    if (!cbaa::bin_ws_make(G, (uint32_t)n_cubes, dev_ws, ws_bytes, &W)) return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_update_segments(G, S, total, W, current_tuning(), as_stream(stream)));
 }
 
 int cbaa_cube_update_binned(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *dev_ws, size_t ws_bytes,
                             void *stream) {
     if (!cube) return CBAA_ERR_INVALID_ARG;
     if (n == 0) return CBAA_OK;
-    if (!dev_pairs || (reinterpret_cast<uintptr_t>(dev_pairs) & 7u)) return CBAA_ERR_INVALID_ARG;
-    if (!dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u)) return CBAA_ERR_INVALID_ARG;
-    if (cbaa::bin_count(cube->G) > cbaa::kMaxBins) return CBAA_ERR_INVALID_ARG;
-    cbaa::BinWs W;
-    if (!cbaa::bin_ws_make(cube->G, dev_ws, ws_bytes, &W)) return CBAA_ERR_INVALID_ARG;
-    return cbaa::launch_update_binned(cube->G, cube->data, dev_pairs, n, W, as_stream(stream)) == cudaSuccess
-               ? CBAA_OK
-               : CBAA_ERR_CUDA;
+    cbaa_cube *cubes[1] = {cube};
+    const uint32_t *pp[1] = {dev_pairs};
+    const size_t nn[1] = {n};
+    return cbaa_cube_update_multi(cubes, 1, pp, nn, dev_ws, ws_bytes, stream);
+}
+
+int cbaa_set_tuning(const cbaa_tuning *t) {
+    if (!t || t->scatter_shape > 4 || t->count_blocks_per_sm > 64 || t->apply_items_per_sm > 1024 ||
+        t->direct_blocks_per_sm > 64)
+        return CBAA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    g_tuning = *t;
+    return CBAA_OK;
+}
+
+int cbaa_get_tuning(cbaa_tuning *t) {
+    if (!t) return CBAA_ERR_INVALID_ARG;
+    *t = current_tuning();
+    return CBAA_OK;
 }
 
 int cbaa_cube_merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream) {
@@ -198,8 +271,8 @@ int cbaa_cube_merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *s
             if (std::memcmp(&s->p, &dst->p, sizeof(cbaa_params)) != 0) return CBAA_ERR_GEOMETRY;
             ptrs[j] = s->data;
         }
-        if (cbaa::launch_merge(dst->data, ptrs, kk, dst->G.cube_words, as_stream(stream)) != cudaSuccess)
-            return CBAA_ERR_CUDA;
+        const int st = cuda_status(cbaa::launch_merge(dst->data, ptrs, kk, dst->G.cube_words, as_stream(stream)));
+        if (st != CBAA_OK) return st;
     }
     return CBAA_OK;
 }
@@ -208,10 +281,7 @@ int cbaa_column_stats(const cbaa_cube *cube, uint32_t theta, uint16_t *dev_zc, u
                       int64_t *dev_zmax, void *stream) {
     if (!cube || !dev_za) return CBAA_ERR_INVALID_ARG;
     const double E = std::exp(-((double)theta / (double)cube->G.g));
-    return cbaa::launch_column_stats(cube->G, cube->data, dev_zc, dev_za, dev_eps, dev_zmax, E, as_stream(stream)) ==
-                   cudaSuccess
-               ? CBAA_OK
-               : CBAA_ERR_CUDA;
+    return cuda_status(cbaa::launch_column_stats(cube->G, cube->data, dev_zc, dev_za, dev_eps, dev_zmax, E, as_stream(stream)));
 }
 
 int cbaa_detect_async(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_bytes, cbaa_host *dev_out,

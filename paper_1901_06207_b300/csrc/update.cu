@@ -199,12 +199,13 @@ int num_sms() {
 
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_update(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, cudaStream_t s) {
+cudaError_t launch_update(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, uint32_t blocks_per_sm,
+                          cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     constexpr int U = 2;
     const uint64_t n2 = n / 2 + 1;
     uint64_t want = (n2 + 255) / 256;
-    const uint64_t cap = (uint64_t)num_sms() * 8;    // 8 x 256 threads per SM
+    const uint64_t cap = (uint64_t)num_sms() * (blocks_per_sm ? blocks_per_sm : 8);   // 256-thread blocks per SM
     const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
     if (G.n_ra == 3 && G.n_va == 1)
         k_update<3, 1, U><<<blocks, 256, 0, s>>>(G, cube, pairs, n);

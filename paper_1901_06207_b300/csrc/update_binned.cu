@@ -1,5 +1,6 @@
-// Alg. 1 by partition: the same cube as the direct update, built without
-// L2 atomics on the cube.
+// Alg. 1 by partition: the same cube bits as the direct update, set without
+// L2 atomics on hot columns.  One pass can feed several cubes of the same
+// geometry (the routers of Section III.C), each from its own packet segments.
 //
 // Why: Alg. 1 sets |RA|+|VA| single bits per packet.  Done as reductions
 // straight into an L2-resident cube, heavy sources (a Zipf head of
@@ -7,22 +8,29 @@
 // L2 lines -- and the reductions on one line serialise.  Here each bit set
 // becomes a 4-byte code routed to the 128 KiB cube tile that holds its
 // word; each tile is then assembled in shared memory, where a hot column's
-// 32 words sit in 32 different banks, and ORed into the cube with one
+// 32 words sit in 32 different banks, and ORed into its cube with one
 // coalesced reduction per non-zero word.
 //
-//   1. k_bin_count   : histogram of codes per tile (shared-memory counters;
-//                      the tile depends on the source address only)
+// Tiles: router cube r owns tiles [r*T, (r+1)*T) with T = ceil(cube words /
+// 2^15); a column never straddles a tile (columns start at multiples of W,
+// tiles are multiples of W words), so a bit's tile depends on the source
+// address only.
+//
+//   1. k_bin_count   : histogram of codes per tile (shared-memory counters)
 //   2. k_bin_scan    : exclusive scans -> code offsets per tile, and apply
 //                      items (a tile's codes cut into chunks of `ch`)
-//   3. k_bin_scatter : each block routes the codes of 4096 packets (kept in
-//                      registers): counts them per tile, reserves one run per
-//                      tile in the code buffer, stages them grouped by tile
-//                      in shared memory and writes the runs out coalesced
+//   3. k_bin_scatter : each block routes the codes of one chunk of packets
+//                      (kept in registers): counts them per tile, reserves
+//                      one run per tile in the code buffer, stages them
+//                      grouped by tile in shared memory and writes the runs
+//                      out coalesced
 //   4. k_bin_apply   : per item: zero a shared tile, set the item's bits
 //                      with shared-memory atomics, OR the non-zero words
-//                      into the cube
+//                      into the tile's cube
 // Traffic per packet: 8 B read twice (count, scatter), 4 B per code
 // written and read once.
+#include <mutex>
+
 #include "cbaa_internal.cuh"
 #include "update_binned.h"
 
@@ -32,8 +40,6 @@ namespace {
 
 constexpr uint32_t kTileBits = kBinTileBits;          // 2^15 words = 128 KiB per tile
 constexpr uint32_t kTileWords = 1u << kTileBits;
-constexpr uint32_t kScatterThreads = 512;
-constexpr uint32_t kScatterPairs = 4096;               // packets per scatter block
 constexpr uint32_t kCountThreads = 256;
 constexpr uint32_t kApplyThreads = 1024;
 
@@ -64,9 +70,17 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
     asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-// Word index of each of the pair's |RA|+|VA| bits (Alg. 1) and the bit.
+// Segment of flattened packet p (segments are few; a linear walk).
+__device__ __forceinline__ uint32_t seg_of(const BinSegs &S, uint64_t p) {
+    uint32_t s = 0;
+    while (s + 1 < S.k && p >= S.start[s + 1]) ++s;
+    return s;
+}
+
+// Word in the tile space (router r's words start at r * seg_words) of each
+// of the pair's |RA|+|VA| bits (Alg. 1), and the bit.
 template <int NRA, int NVA>
-__device__ __forceinline__ uint32_t pair_targets(const Geo &G, uint32_t iip, uint32_t oip,
+__device__ __forceinline__ uint32_t pair_targets(const Geo &G, uint32_t seg_base, uint32_t iip, uint32_t oip,
                                                  uint32_t (&w)[NRA ? NRA + NVA : CBAA_MAX_ARRAYS], uint32_t &bit) {
     const uint32_t nra = NRA ? NRA : G.n_ra;
     const uint32_t nva = NRA ? NVA : G.n_va;
@@ -74,7 +88,7 @@ __device__ __forceinline__ uint32_t pair_targets(const Geo &G, uint32_t iip, uin
     const uint32_t m = mangle(G, iip);
     const uint32_t cs = m & G.smask;
     const uint32_t lp = m >> G.r;
-    const uint32_t base = cs * G.cs_words + (row >> 5);
+    const uint32_t base = seg_base + cs * G.cs_words + (row >> 5);
 #pragma unroll
     for (uint32_t i = 0; i < (NRA ? NRA : CBAA_MAX_RA); ++i) {
         if (NRA == 0 && i >= nra) break;
@@ -89,18 +103,16 @@ __device__ __forceinline__ uint32_t pair_targets(const Geo &G, uint32_t iip, uin
     return nra + nva;
 }
 
-// Tile of each of the pair's bits.  A column never straddles a tile (columns
-// start at multiples of W and a tile is a multiple of W words), so the tile
-// depends on the source address only and the row hash is not needed here.
+// Tile of each of the pair's bits (source address only, see above).
 template <int NRA, int NVA>
-__device__ __forceinline__ uint32_t source_tiles(const Geo &G, uint32_t iip,
+__device__ __forceinline__ uint32_t source_tiles(const Geo &G, uint32_t seg_base, uint32_t iip,
                                                  uint32_t (&t)[NRA ? NRA + NVA : CBAA_MAX_ARRAYS]) {
     const uint32_t nra = NRA ? NRA : G.n_ra;
     const uint32_t nva = NRA ? NVA : G.n_va;
     const uint32_t m = mangle(G, iip);
     const uint32_t cs = m & G.smask;
     const uint32_t lp = m >> G.r;
-    const uint32_t base = cs * G.cs_words;
+    const uint32_t base = seg_base + cs * G.cs_words;
 #pragma unroll
     for (uint32_t i = 0; i < (NRA ? NRA : CBAA_MAX_RA); ++i) {
         if (NRA == 0 && i >= nra) break;
@@ -151,16 +163,17 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
 }
 
 template <int NRA, int NVA>
-__global__ void __launch_bounds__(kCountThreads) k_bin_count(const Geo G, const uint32_t *__restrict__ pairs,
-                                                             uint64_t n, uint32_t nb, uint32_t *__restrict__ counts) {
+__global__ void __launch_bounds__(kCountThreads) k_bin_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
+                                                             uint32_t *__restrict__ counts) {
     extern __shared__ uint32_t hist[];
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-        const uint32_t iip = ld_stream_u32(pairs + 2 * p);
+        const uint32_t s = seg_of(S, p);
+        const uint32_t iip = ld_stream_u32(S.pairs[s] + 2 * (p - S.start[s]));
         uint32_t t[NRA ? NRA + NVA : CBAA_MAX_ARRAYS];
-        const uint32_t A = source_tiles<NRA, NVA>(G, iip, t);
+        const uint32_t A = source_tiles<NRA, NVA>(G, S.router[s] * S.seg_words, iip, t);
 #pragma unroll
         for (uint32_t a = 0; a < (NRA ? NRA + NVA : CBAA_MAX_ARRAYS); ++a) {
             if (NRA == 0 && a >= A) break;
@@ -189,34 +202,36 @@ __global__ void __launch_bounds__(1024) k_bin_scan(const uint32_t *__restrict__ 
     if (threadIdx.x == 0) item_start[nb] = items;
 }
 
-template <int NRA, int NVA>
-__global__ void __launch_bounds__(kScatterThreads) k_bin_scatter(const Geo G, const uint32_t *__restrict__ pairs,
-                                                                 uint64_t n, uint32_t nb,
-                                                                 uint32_t *__restrict__ cursors,
-                                                                 uint32_t *__restrict__ codes) {
+// THREADS x PPT packets per block.
+template <int NRA, int NVA, int THREADS, int PPT>
+__global__ void __launch_bounds__(THREADS) k_bin_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
+                                                         uint32_t *__restrict__ cursors,
+                                                         uint32_t *__restrict__ codes) {
     extern __shared__ uint32_t sm[];
-    uint32_t *hist = sm;             // per-tile count, then fill position
-    uint32_t *lstart = sm + nb;      // start of each tile's run in `staged`
-    uint32_t *gbase = sm + 2 * nb;   // start of each tile's run in `codes`
+    uint32_t *hist = sm;             // per-tile count
+    uint32_t *fill = sm + nb;        // next free slot of each tile's run in `staged`
+    uint32_t *delta = sm + 2 * nb;   // run start in `codes` minus run start in `staged`
     uint32_t *staged = sm + 3 * nb;  // codes of this block, grouped by tile
     __shared__ uint32_t tmp[32];
     constexpr uint32_t AM = NRA ? NRA + NVA : CBAA_MAX_ARRAYS;
-    constexpr uint32_t PPT = kScatterPairs / kScatterThreads;     // packets per thread
-    const uint64_t p0 = (uint64_t)blockIdx.x * kScatterPairs;
-    const uint32_t np = (uint32_t)((n - p0) < kScatterPairs ? (n - p0) : kScatterPairs);
+    constexpr uint32_t P = THREADS * PPT;
+    const uint64_t p0 = (uint64_t)blockIdx.x * P;
+    const uint32_t np = (uint32_t)((n - p0) < P ? (n - p0) : P);
 
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    for (uint32_t i = threadIdx.x; i < nb; i += THREADS) hist[i] = 0;
     __syncthreads();
     // codes packed as tile << (kTileBits + 5) | word-in-tile << 5 | bit, kept in registers
     uint32_t code[PPT][AM];
     uint32_t A = G.A;
 #pragma unroll
     for (uint32_t k = 0; k < PPT; ++k) {
-        const uint32_t p = threadIdx.x + k * kScatterThreads;
+        const uint32_t p = threadIdx.x + k * THREADS;
         if (p < np) {
-            const uint2 v = ld_pair(pairs + 2 * (p0 + p));
+            const uint64_t gp = p0 + p;
+            const uint32_t s = seg_of(S, gp);
+            const uint2 v = ld_pair(S.pairs[s] + 2 * (gp - S.start[s]));
             uint32_t w[AM], bit;
-            A = pair_targets<NRA, NVA>(G, v.x, v.y, w, bit);
+            A = pair_targets<NRA, NVA>(G, S.router[s] * S.seg_words, v.x, v.y, w, bit);
 #pragma unroll
             for (uint32_t a = 0; a < AM; ++a) {
                 if (NRA == 0 && a >= A) break;
@@ -227,35 +242,32 @@ __global__ void __launch_bounds__(kScatterThreads) k_bin_scatter(const Geo G, co
         }
     }
     __syncthreads();
-    const uint32_t total = block_exclusive_scan(hist, lstart, nb, tmp);
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+    const uint32_t total = block_exclusive_scan(hist, fill, nb, tmp);
+    for (uint32_t b = threadIdx.x; b < nb; b += THREADS) {
         const uint32_t c = hist[b];
-        if (c) gbase[b] = atomicAdd(&cursors[b], c);
-        hist[b] = 0;
+        if (c) delta[b] = atomicAdd(&cursors[b], c) - fill[b];
     }
     __syncthreads();
 #pragma unroll
     for (uint32_t k = 0; k < PPT; ++k) {
-        const uint32_t p = threadIdx.x + k * kScatterThreads;
+        const uint32_t p = threadIdx.x + k * THREADS;
         if (p < np) {
 #pragma unroll
             for (uint32_t a = 0; a < AM; ++a) {
                 if (NRA == 0 && a >= A) break;
                 const uint32_t v = code[k][a];
-                const uint32_t b = v >> (kTileBits + 5);
-                staged[lstart[b] + atomicAdd(&hist[b], 1u)] = v;
+                staged[atomicAdd(&fill[v >> (kTileBits + 5)], 1u)] = v;
             }
         }
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < total; t += blockDim.x) {
+    for (uint32_t t = threadIdx.x; t < total; t += THREADS) {
         const uint32_t v = staged[t];
-        const uint32_t b = v >> (kTileBits + 5);
-        codes[gbase[b] + (t - lstart[b])] = v;
+        codes[delta[v >> (kTileBits + 5)] + t] = v;
     }
 }
 
-__global__ void __launch_bounds__(kApplyThreads) k_bin_apply(uint32_t *__restrict__ cube, uint64_t cube_words,
+__global__ void __launch_bounds__(kApplyThreads) k_bin_apply(const BinSegs S, uint64_t cube_words,
                                                              const uint32_t *__restrict__ codes,
                                                              const uint32_t *__restrict__ offsets,
                                                              const uint32_t *__restrict__ item_start, uint32_t nb,
@@ -279,10 +291,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_bin_apply(uint32_t *__restric
         const uint32_t up4 = (c0 + 3u) & ~3u;
         const uint32_t a0 = up4 < c1 ? up4 : c1;
         const uint32_t a1 = a0 + ((c1 - a0) & ~3u);
-        for (uint32_t c = c0 + threadIdx.x; c < a0; c += blockDim.x) {
-            const uint32_t v = ld_stream_u32(codes + c);
-            atomicOr(&tile[(v >> 5) & (kTileWords - 1u)], 1u << (v & 31u));
-        }
+        for (uint32_t c = c0 + threadIdx.x; c < a0; c += blockDim.x) apply_code(tile, ld_stream_u32(codes + c));
         const uint4 *q = reinterpret_cast<const uint4 *>(codes + a0);
         const uint32_t nq = (a1 - a0) / 4;
         uint32_t i = threadIdx.x;
@@ -297,50 +306,109 @@ __global__ void __launch_bounds__(kApplyThreads) k_bin_apply(uint32_t *__restric
         }
         for (uint32_t c = a1 + threadIdx.x; c < c1; c += blockDim.x) apply_code(tile, ld_stream_u32(codes + c));
         __syncthreads();
-        const uint64_t base = (uint64_t)b << kTileBits;
+        const uint32_t r = b / S.tiles_per_seg;
+        const uint64_t base = (uint64_t)(b - r * S.tiles_per_seg) << kTileBits;   // inside cube r
         const uint32_t lim = (uint32_t)((cube_words - base) < kTileWords ? (cube_words - base) : kTileWords);
-        for (uint32_t i = threadIdx.x; i < lim; i += blockDim.x) {
-            const uint32_t v = tile[i];
-            if (v) red_or(cube + base + i, v);
+        uint32_t *dst = S.cube[r] + base;
+        for (uint32_t w = threadIdx.x; w < lim; w += blockDim.x) {
+            const uint32_t v = tile[w];
+            if (v) red_or(dst + w, v);
         }
         __syncthreads();
     }
 }
 
+// Opt a kernel into `bytes` of dynamic shared memory once per device and
+// kernel (again only if a larger size is asked for), so that launches
+// recorded into a CUDA graph do not repeat the attribute call.
+std::mutex g_smem_mu;
+struct SmemGrant { const void *fn; int dev; size_t bytes; };
+SmemGrant g_smem[128];
+int g_smem_n = 0;
+
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const void *fn = reinterpret_cast<const void *>(kernel);
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    int i = 0;
+    for (; i < g_smem_n; ++i)
+        if (g_smem[i].fn == fn && g_smem[i].dev == dev) break;
+    if (i < g_smem_n && g_smem[i].bytes >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (i == g_smem_n) {
+        if (g_smem_n == 128) return cudaSuccess;       // table full: the attribute is set, just not remembered
+        g_smem[g_smem_n++] = {fn, dev, bytes};
+    } else {
+        g_smem[i].bytes = bytes;
+    }
+    return cudaSuccess;
+}
+
+template <int NRA, int NVA, int THREADS, int PPT>
+cudaError_t launch_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W, cudaStream_t s) {
+    const size_t smem = sizeof(uint32_t) * (3ull * nb + (size_t)G.A * THREADS * PPT);
+    cudaError_t e = allow_smem(k_bin_scatter<NRA, NVA, THREADS, PPT>, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
+    k_bin_scatter<NRA, NVA, THREADS, PPT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes);
+    return cudaGetLastError();
 }
 
 template <int NRA, int NVA>
-cudaError_t launch_binned_t(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, const BinWs &W,
+cudaError_t launch_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
+                                 uint32_t shape, cudaStream_t s) {
+    switch (shape) {
+        case 1: return launch_scatter<NRA, NVA, 512, 4>(G, S, m, nb, W, s);
+        case 2: return launch_scatter<NRA, NVA, 1024, 4>(G, S, m, nb, W, s);
+        case 3: return launch_scatter<NRA, NVA, 256, 8>(G, S, m, nb, W, s);
+        case 4: return launch_scatter<NRA, NVA, 256, 4>(G, S, m, nb, W, s);
+        default: return launch_scatter<NRA, NVA, 512, 8>(G, S, m, nb, W, s);
+    }
+}
+
+template <int NRA, int NVA>
+cudaError_t launch_binned_t(const Geo &G, const BinSegs &S0, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                             cudaStream_t s) {
-    const uint32_t nb = bin_count(G);
+    const uint32_t nb = S0.n_routers * S0.tiles_per_seg;
     const uint32_t A = G.A;
     const int sms = num_sms();
-    const size_t scatter_smem = sizeof(uint32_t) * (3ull * nb + (size_t)A * kScatterPairs);
     const size_t apply_smem = sizeof(uint32_t) * kTileWords;
     cudaError_t e;
-    if ((e = allow_smem(k_bin_scatter<NRA, NVA>, scatter_smem)) != cudaSuccess) return e;
     if ((e = allow_smem(k_bin_apply, apply_smem)) != cudaSuccess) return e;
     if ((e = allow_smem(k_bin_count<NRA, NVA>, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
-    for (size_t done = 0; done < n;) {
-        const size_t m = (n - done) < W.max_pairs ? (n - done) : W.max_pairs;
-        const uint32_t *pp = pairs + 2 * done;
+    const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
+    const uint32_t apply_ips = T.apply_items_per_sm ? T.apply_items_per_sm : 8;
+    for (uint64_t done = 0; done < n;) {
+        const uint64_t m = (n - done) < W.max_pairs ? (n - done) : W.max_pairs;
+        // the segments clipped to flattened packets [done, done + m), re-based at 0
+        BinSegs S = S0;
+        S.k = 0;
+        for (uint32_t j = 0; j < S0.k; ++j) {
+            const uint64_t a = S0.start[j] > done ? S0.start[j] : done;
+            const uint64_t b = S0.start[j + 1] < done + m ? S0.start[j + 1] : done + m;
+            if (a >= b) continue;
+            S.pairs[S.k] = S0.pairs[j] + 2 * (a - S0.start[j]);
+            S.start[S.k] = a - done;
+            S.router[S.k] = S0.router[j];
+            ++S.k;
+        }
+        S.start[S.k] = m;
         if ((e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * nb, s)) != cudaSuccess) return e;
         const uint64_t want = (m + kCountThreads - 1) / kCountThreads;
-        const unsigned cblocks = (unsigned)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
-        k_bin_count<NRA, NVA><<<cblocks, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, pp, m, nb, W.counts);
+        const uint64_t cap = (uint64_t)sms * count_bps;
+        const unsigned cblocks = (unsigned)(want < cap ? want : cap);
+        k_bin_count<NRA, NVA><<<cblocks, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        // apply items: about 8 per SM, at least 16 Ki codes each
-        uint64_t ch = ((uint64_t)A * m + (uint64_t)sms * 8 - 1) / ((uint64_t)sms * 8);
+        uint64_t ch = ((uint64_t)A * m + (uint64_t)sms * apply_ips - 1) / ((uint64_t)sms * apply_ips);
         if (ch < (1u << 14)) ch = 1u << 14;
         k_bin_scan<<<1, 1024, 0, s>>>(W.counts, nb, (uint32_t)ch, W.offsets, W.cursors, W.item_start, W.nchunk);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const unsigned sblocks = (unsigned)((m + kScatterPairs - 1) / kScatterPairs);
-        k_bin_scatter<NRA, NVA><<<sblocks, kScatterThreads, scatter_smem, s>>>(G, pp, m, nb, W.cursors, W.codes);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_bin_apply<<<(unsigned)sms, kApplyThreads, apply_smem, s>>>(cube, G.cube_words, W.codes, W.offsets,
+        if ((e = launch_scatter_shape<NRA, NVA>(G, S, m, nb, W, T.scatter_shape, s)) != cudaSuccess) return e;
+        k_bin_apply<<<(unsigned)sms, kApplyThreads, apply_smem, s>>>(S, G.cube_words, W.codes, W.offsets,
                                                                      W.item_start, nb, (uint32_t)ch);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         done += m;
@@ -350,11 +418,11 @@ cudaError_t launch_binned_t(const Geo &G, uint32_t *cube, const uint32_t *pairs,
 
 }  // namespace
 
-cudaError_t launch_update_binned(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, const BinWs &W,
-                                 cudaStream_t s) {
+cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
+                                   cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    if (G.n_ra == 3 && G.n_va == 1) return launch_binned_t<3, 1>(G, cube, pairs, n, W, s);
-    return launch_binned_t<0, 0>(G, cube, pairs, n, W, s);
+    if (G.n_ra == 3 && G.n_va == 1) return launch_binned_t<3, 1>(G, S, n, W, T, s);
+    return launch_binned_t<0, 0>(G, S, n, W, T, s);
 }
 
 }  // namespace cbaa

@@ -1,4 +1,4 @@
-// Workspace of the partitioned (binned) update: host arithmetic + pointers.
+// Partitioned (binned) update: tile-space description, workspace, launch.
 #pragma once
 
 #include <stddef.h>
@@ -9,11 +9,26 @@
 namespace cbaa {
 
 constexpr uint32_t kBinTileBits = 15;     // one tile = 2^15 cube words (128 KiB)
-constexpr uint32_t kMaxBins = 4096;       // tile id fits the top 12 bits of a code: cube <= 512 MiB
+constexpr uint32_t kMaxBins = 4096;       // tile id fits the top 12 bits of a code: <= 512 MiB of cubes
+constexpr uint32_t kMaxRouters = 16;      // cubes fed by one pass
+constexpr uint32_t kMaxSegs = 32;         // packet segments of one pass
 
-inline uint32_t bin_count(const Geo &G) {
+inline uint32_t tiles_per_cube(const Geo &G) {
     return (uint32_t)((G.cube_words + (1ull << kBinTileBits) - 1) >> kBinTileBits);
 }
+
+// Packets of one pass: segment j holds packets [start[j], start[j+1]) of the
+// flattened pass, read from pairs[j], and feeds cube[router[j]].
+struct BinSegs {
+    const uint32_t *pairs[kMaxSegs];
+    uint64_t start[kMaxSegs + 1];
+    uint32_t router[kMaxSegs];
+    uint32_t *cube[kMaxRouters];
+    uint32_t k;               // segments
+    uint32_t n_routers;       // cubes
+    uint32_t tiles_per_seg;   // tiles per cube
+    uint32_t seg_words;       // tiles_per_seg << kBinTileBits: offset between cubes in the tile space
+};
 
 struct BinWs {
     uint32_t *counts, *offsets, *cursors, *item_start, *nchunk, *codes;
@@ -24,13 +39,13 @@ inline size_t bin_align(size_t x) { return (x + 255) / 256 * 256; }
 
 inline size_t bin_ws_fixed(uint32_t nb) { return 5 * bin_align(sizeof(uint32_t) * ((size_t)nb + 1)); }
 
-inline size_t bin_ws_bytes(const Geo &G, size_t max_pairs) {
-    return bin_ws_fixed(bin_count(G)) + bin_align(sizeof(uint32_t) * (size_t)G.A * max_pairs);
+inline size_t bin_ws_bytes(const Geo &G, uint32_t n_cubes, size_t max_pairs) {
+    return bin_ws_fixed(n_cubes * tiles_per_cube(G)) + bin_align(sizeof(uint32_t) * (size_t)G.A * max_pairs);
 }
 
-// Carve `bytes` at `base` into a BinWs; false if not even one packet fits.
-inline bool bin_ws_make(const Geo &G, void *base, size_t bytes, BinWs *W) {
-    const uint32_t nb = bin_count(G);
+// Carve `bytes` at `base` into a BinWs for n_cubes cubes; false if not even one packet fits.
+inline bool bin_ws_make(const Geo &G, uint32_t n_cubes, void *base, size_t bytes, BinWs *W) {
+    const uint32_t nb = n_cubes * tiles_per_cube(G);
     const size_t fixed = bin_ws_fixed(nb);
     if (bytes < fixed + sizeof(uint32_t) * G.A) return false;
     size_t m = (bytes - fixed) / (sizeof(uint32_t) * G.A);
@@ -48,7 +63,7 @@ inline bool bin_ws_make(const Geo &G, void *base, size_t bytes, BinWs *W) {
     return true;
 }
 
-cudaError_t launch_update_binned(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, const BinWs &W,
-                                 cudaStream_t s);
+cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
+                                   cudaStream_t s);
 
 }  // namespace cbaa

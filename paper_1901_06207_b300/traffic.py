@@ -232,3 +232,12 @@ def split_by_router(pairs: np.ndarray, seed: int, n_routers: int, sigma: float =
     u = (h >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
     rid = np.searchsorted(np.cumsum(w), u, side="right")
     return np.minimum(rid, n_routers - 1).astype(np.uint8), w
+
+
+def router_window(spec: TrafficSpec, n_routers: int, sigma: float = 0.8):
+    """A window split over n_routers edge routers: (packets grouped by router, packets per router, weights)."""
+    w = make_window(spec)
+    rid, weights = split_by_router(w.pairs, spec.seed, n_routers, sigma)
+    order = np.argsort(rid, kind="stable")
+    counts = np.bincount(rid, minlength=n_routers).astype(np.int64)
+    return np.ascontiguousarray(w.pairs[order]), counts, weights

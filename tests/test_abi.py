@@ -108,3 +108,21 @@ def test_update_workspace_limits(C):
     big = C.make_params(8, 3, 1, 10, [13])          # 1 GiB cube
     assert C.validate(big) == C.OK and C.update_workspace_bytes(big, 1024) == 0
     assert C.update_workspace_bytes(GEO.L2, 0) == 0
+
+
+def test_tuning_roundtrip_and_limits(C):
+    before = C.get_tuning()
+    C.set_tuning(scatter_shape=3, count_blocks_per_sm=4, apply_items_per_sm=16, direct_blocks_per_sm=2)
+    assert C.get_tuning() == dict(scatter_shape=3, count_blocks_per_sm=4, apply_items_per_sm=16,
+                                  direct_blocks_per_sm=2)
+    with pytest.raises(C.CbaaError):
+        C.set_tuning(scatter_shape=9)
+    C.set_tuning(**before)
+    assert C.get_tuning() == before
+
+
+def test_multi_workspace_limits(C):
+    assert C.update_multi_workspace_bytes(GEO.L2, 8, 1 << 20) > C.update_multi_workspace_bytes(GEO.L2, 1, 1 << 20)
+    assert C.update_multi_workspace_bytes(GEO.L2, 9, 1 << 20) == 0        # 9 x 64 MiB > 512 MiB
+    assert C.update_multi_workspace_bytes(GEO.TINY, 16, 1 << 10) > 0
+    assert C.update_multi_workspace_bytes(GEO.TINY, 17, 1 << 10) == 0

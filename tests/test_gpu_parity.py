@@ -105,6 +105,38 @@ def test_binned_update_passes_ragged_and_incremental(C, oracle):
     assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
+def test_binned_update_every_scatter_shape(C, oracle, shape):
+    """Launch shapes change timing only: every routing shape gives the oracle's cube."""
+    d = GEO.L2
+    w = window("4m")
+    before = C.get_tuning()
+    try:
+        C.set_tuning(scatter_shape=shape, count_blocks_per_sm=2 + shape, apply_items_per_sm=1 + 3 * shape)
+        cube = C.Cube(d)
+        cube.update_binned(dev_pairs(w.pairs), C.UpdateWorkspace(d, w.pairs.shape[0]))
+        assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
+    finally:
+        C.set_tuning(**before)
+
+
+@pytest.mark.parametrize("geo,win,k", [("TINY2", "tiny", 5), ("L2", "4m", 8), ("TINY", "tiny", 16)])
+def test_multi_router_update(C, oracle, geo, win, k):
+    """One partitioned pass over k router cubes: each equals the oracle cube of its own packets."""
+    d = GEO.ALL[geo]
+    w = window(win)
+    rid, _ = T.split_by_router(w.pairs, 91, k)
+    parts = [w.pairs[rid == j] for j in range(k)]
+    cubes = [C.Cube(d) for _ in range(k)]
+    ws = C.UpdateWorkspace(d, max(1, w.pairs.shape[0] // 3), n_cubes=k)     # several passes
+    C.update_multi(cubes, [dev_pairs(p) if p.size else None for p in parts], ws)
+    for j in range(k):
+        assert np.array_equal(cubes[j].to_numpy(), oracle.build_cube(d, parts[j])), j
+    glob = C.Cube(d)
+    glob.merge(cubes)
+    assert np.array_equal(glob.to_numpy(), oracle.build_cube(d, w.pairs))
+
+
 def test_update_ragged_and_unaligned(C, oracle):
     """Odd counts, a start that is only 8-byte aligned, empty and one-pair calls, uneven batches."""
     import torch
