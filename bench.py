@@ -515,13 +515,103 @@ def run_batched(args):
     return 0
 
 
+def serve_schedule(n_pool: int, rate_pps: float, horizon_s: float, seed: int = 0xC0FFEE30):
+    """Batches (offset into the packet pool, size) and Poisson arrival times at rate_pps for horizon_s."""
+    out, t, off, i = [], 0.0, 0, 0
+    while t < horizon_s:
+        u = T.rand_unit(seed, 11, 2, 2 * i)
+        size = int(np.exp(np.log(1 << 16) + u[0] * (np.log(4 << 20) - np.log(1 << 16))))
+        t += -np.log(max(u[1], 1e-12)) * size / rate_pps
+        if off + size > n_pool:
+            off = 0
+        out.append((off, size, t))
+        off += size
+        i += 1
+    return out
+
+
+def run_serve(args):
+    """Serving: uneven batches through the continuous-batching server into 1 s windows.  A paced run
+    at the target rate gives window latency; an unpaced run gives the server's capacity."""
+    rank, world, local = dist_env()
+    import torch
+    from paper_1901_06207_b300 import cbaa as C
+    from paper_1901_06207_b300.serve import Server
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    geo = C.make_params(6, 3, 1, 10, [13])                        # 256 MiB cubes for ~200M-packet windows
+    theta = 1024
+    w = T.make_window(T.spec_window_64m(seed=0xC0FFEE30 + 0x100 * rank))
+    pool = torch.from_numpy(w.pairs.view(np.int32)).pin_memory()
+    n_pool = pool.shape[0]
+    rate = args.serve_rate
+    srv = Server(geo, theta, n_slots=4, slot_pairs=4 << 20, n_cubes=4, device=dev)
+
+    def run(schedule, paced: bool):
+        srv.results.clear()
+        t0 = time.perf_counter()
+        cur = 0
+        for off, size, t_arr in schedule:
+            win = int(t_arr // args.serve_window_s)
+            if paced:
+                while time.perf_counter() - t0 < t_arr:
+                    srv.poll()
+            if win != cur:
+                srv.close(0, cur)
+                cur = win
+            srv.submit(0, win, pool[off:off + size], arrival_t=t0 + t_arr)
+        srv.close(0, cur)
+        res = srv.drain(timeout_s=300)
+        torch.cuda.synchronize()
+        return res, time.perf_counter() - t0
+
+    warm = serve_schedule(n_pool, rate, 0.2 * args.serve_window_s, seed=0xC0FFEE31)
+    run(warm, paced=False)
+    paced_sched = serve_schedule(n_pool, rate, args.serve_windows * args.serve_window_s)
+    with ClockSampler(local) as clocks:
+        res_p, el_p = run(paced_sched, paced=True)
+    lat = sorted(r.latency_s * 1e3 for r in res_p)
+    cap_sched = serve_schedule(n_pool, rate, args.serve_windows * args.serve_window_s, seed=0xC0FFEE32)
+    res_c, el_c = run(cap_sched, paced=False)
+    pk_p = sum(r.packets for r in res_p)
+    pk_c = sum(r.packets for r in res_c)
+    cap_gpps = reduce_over_ranks(pk_c, world, "sum", dev) / reduce_over_ranks(el_c, world, "max", dev) / 1e9
+    line = {"metric": METRIC, "value": cap_gpps, "unit": "Gpps", "n_gpus": world, "steps": len(res_c),
+            "warmup": 1, "ms_per_step": 1e3 * el_c / max(1, len(res_c)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "serve_200mpps_1s_windows",
+                       "batches": "log-uniform sizes in [64Ki, 4Mi] pairs cut from a 64M-packet window",
+                       "arrivals": f"Poisson at {rate / 1e6:.0f} Mpps", "window_s": args.serve_window_s,
+                       "geometry": "r=6, |RA|=3, |VA|=1, g=2^10, c=2^13 (256 MiB cubes)", "theta": theta,
+                       "server": "4 staging slots of 4Mi pairs, 4 cube buffers, copy/compute/detect streams",
+                       "value": "unpaced capacity: host batches -> H2D -> update -> windows -> host lists"},
+            "paced": {"offered_mpps": rate / 1e6, "sustained_gpps": pk_p / el_p / 1e9, "windows": len(res_p),
+                      "latency_ms_p50": lat[len(lat) // 2] if lat else None,
+                      "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+                      "latency": "window close -> host list on the host"},
+            "capacity": {"packets": pk_c, "seconds": el_c, "windows": len(res_c)},
+            "server_stats": dict(srv.stats),
+            "hosts_per_window": [int(r.info["n_hosts"]) for r in res_p],
+            "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cbaa", "reference"], default="cbaa")
-    ap.add_argument("--workload", default="window64m", choices=["window64m", "window1m", "batched"])
+    ap.add_argument("--workload", default="window64m", choices=["window64m", "window1m", "batched", "serve"])
+    ap.add_argument("--serve-rate", type=float, default=2e8, help="serve workload: offered packets/s")
+    ap.add_argument("--serve-window-s", type=float, default=1.0, help="serve workload: window length")
+    ap.add_argument("--serve-windows", type=int, default=3, help="serve workload: windows per run")
     ap.add_argument("--update", default="auto", choices=["auto", "binned", "direct"],
                     help="Alg. 1 path: partitioned by cube tile (binned), RED.OR into the cube (direct), "
                          "or the autotuner's pick (auto)")
@@ -535,7 +625,11 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
-    return run_batched(args) if args.workload == "batched" else run_cbaa(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    return run_cbaa(args)
 
 
 if __name__ == "__main__":

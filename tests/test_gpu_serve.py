@@ -1,0 +1,91 @@
+"""Continuous-batching serving: every (tenant, window) result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+import geometries as GEO
+from paper_1901_06207_b300 import traffic as T
+
+pytestmark = pytest.mark.gpu
+THETA = 128
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1901_06207_b300 import build
+    build.build()
+    from paper_1901_06207_b300 import cbaa
+    return cbaa
+
+
+def _traffic(tenant, window):
+    spec = T.TrafficSpec(n_packets=(1 << 17) + 4099 * tenant, n_hosts=3000, n_planted=120, planted_lo=160,
+                         planted_hi=900, planted_dist="uniform", bg_mode="per_host", zipf_a=1.2, bg_max=64,
+                         seed=0x5E00 + 16 * tenant + window)
+    return T.make_window(spec).pairs
+
+
+def _batches(pairs, seed):
+    """Uneven batch sizes, log-uniform in [2^10, 2^15]."""
+    rng = np.random.default_rng(seed)
+    out, i = [], 0
+    while i < pairs.shape[0]:
+        n = int(np.exp(rng.uniform(np.log(1 << 10), np.log(1 << 15))))
+        out.append(pairs[i:i + n])
+        i += n
+    return out
+
+
+def _pinned(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+
+
+def _run(C, tenants, windows, n_slots, n_cubes, interleave_seed=None):
+    from paper_1901_06207_b300.serve import Server
+    srv = Server(GEO.TINY2, THETA, n_slots=n_slots, slot_pairs=1 << 15, n_cubes=n_cubes, cap=1 << 12)
+    streams = {t: [(w, b) for w in range(windows) for b in _batches(_traffic(t, w), 100 * t + w)] for t in tenants}
+    order = [t for t in tenants for _ in streams[t]]
+    if interleave_seed is not None:
+        np.random.default_rng(interleave_seed).shuffle(order)
+    pos = {t: 0 for t in tenants}
+    for t in order:                       # each tenant's batches stay in order; tenants interleave
+        w, b = streams[t][pos[t]]
+        pos[t] += 1
+        srv.submit(t, w, _pinned(b))
+        if pos[t] == len(streams[t]) or streams[t][pos[t]][0] != w:
+            srv.close(t, w)
+    res = srv.drain(timeout_s=120)
+    return {(r.tenant, r.window): r for r in res}, srv
+
+
+def test_serving_results_same_alone_and_mixed(C, oracle):
+    tenants, windows = [0, 1, 2], 2
+    alone = {}
+    for t in tenants:
+        r, _ = _run(C, [t], windows, n_slots=2, n_cubes=2)
+        alone.update(r)
+    mixed, srv = _run(C, tenants, windows, n_slots=3, n_cubes=2, interleave_seed=7)
+    assert set(mixed) == set(alone) == {(t, w) for t in tenants for w in range(windows)}
+    for key, r in mixed.items():
+        a = alone[key]
+        assert r.info["status"] == C.OK and a.info["status"] == C.OK
+        assert r.packets == a.packets
+        assert np.array_equal(r.hosts, a.hosts), key            # bit-exact, estimates included
+        t, w = key
+        want = oracle.detect(GEO.TINY2, oracle.build_cube(GEO.TINY2, _traffic(t, w)), THETA)["hosts"]
+        assert np.array_equal(r.hosts["ip"], want["ip"]) and np.array_equal(r.hosts["z"], want["z"])
+        assert r.latency_s >= 0
+    # memory-based admission: two cubes for three tenants -- never more in use, and windows had to wait
+    assert srv.stats["max_cubes_in_use"] <= 2
+    assert srv.stats["queued_for_cube"] > 0
+
+
+def test_serving_budget_and_batch_limits(C):
+    from paper_1901_06207_b300.serve import Server
+    with pytest.raises(C.CbaaError):
+        Server(GEO.TINY2, THETA, n_slots=2, slot_pairs=1 << 15, mem_budget=1 << 20)    # no room for a cube
+    srv = Server(GEO.TINY2, THETA, n_slots=1, slot_pairs=1 << 10, n_cubes=1)
+    with pytest.raises(C.CbaaError):
+        srv.submit(0, 0, _pinned(np.zeros((2048, 2), np.uint32)))                     # larger than a slot
