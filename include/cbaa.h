@@ -254,6 +254,61 @@ int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_b
 int cbaa_detect_static(const cbaa_cube *cube, uint32_t theta, cbaa_host *dev_out, size_t cap,
                        cbaa_detect_info *dev_info, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Learned estimator.  The paper estimates with Thm. 2 alone; these calls
+ * add a small network that maps what the cube shows about an address to a
+ * correction y of ln(1 + Thm. 2 estimate) towards ln(1 + |OP(ip)|), for
+ * cubes whose arrays saturate.  Thm. 2 remains the fallback
+ * (cbaa_learned_decide).
+ *
+ * Network: x (16 features) -> 64 ReLU -> 64 ReLU -> 1, weights in BF16,
+ * activations and accumulation in FP32.  Parameters are one flat array in
+ * the order W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3
+ * (CBAA_MLP_PARAMS entries): BF16 (uint16 bit patterns) for the kernels,
+ * FP32 for the optimiser's master copy.
+ */
+#define CBAA_MLP_IN     16
+#define CBAA_MLP_HIDDEN 64
+#define CBAA_MLP_PARAMS 5313
+
+/* Features of n addresses (dev_ips), async, into dev_feats float[n][16]
+ * (16-byte aligned): per array a < 4 the zero fraction of the address's
+ * column (0..3), the zero fraction of the union column (4), the zero
+ * fraction of array a of its sketch (5..8), eps (9), the Thm. 2 estimate / g
+ * (10), ln(1 + estimate) / 10 (11), 1 if the union column is saturated
+ * (12), the smallest column zero fraction (13), ln(ones fraction of the
+ * union) minus the sum over all arrays of ln(ones fraction of the column)
+ * (14; near 0 when the columns are unrelated, as for an address that never
+ * appeared), ln(ones fraction of the union) (15); ones fractions are floored
+ * at 1/g.  dev_za and
+ * dev_eps come from cbaa_column_stats on the same cube. */
+int cbaa_host_features(const cbaa_cube *cube, const uint64_t *dev_za, const double *dev_eps,
+                       const uint32_t *dev_ips, size_t n, float *dev_feats, void *stream);
+
+/* dev_y[s] = network(dev_x[s]) for s < n, async (dev_x float[n][16], 16-byte aligned). */
+int cbaa_mlp_forward(const uint16_t *dev_w_bf16, const float *dev_x, size_t n, float *dev_y, void *stream);
+
+/* Accumulate into dev_grad (float[CBAA_MLP_PARAMS]) the gradient, with
+ * respect to the BF16 weights, of scale * sum_s (y_s - dev_t[s])^2, and add
+ * sum_s (y_s - dev_t[s])^2 to *dev_loss; async.  The caller zeroes both. */
+int cbaa_mlp_grad(const uint16_t *dev_w_bf16, const float *dev_x, const float *dev_t, size_t n, float scale,
+                  float *dev_grad, float *dev_loss, void *stream);
+
+/* One Adam step (Kingma and Ba) on the FP32 master weights with bias
+ * correction for step >= 1, then the BF16 copy is refreshed; async. */
+int cbaa_mlp_adam(float *dev_master, const float *dev_grad, float *dev_m, float *dev_v, uint16_t *dev_w_bf16,
+                  float lr, float beta1, float beta2, float eps, uint32_t step, void *stream);
+
+/* dev_w_bf16 = round-to-nearest-even BF16 of dev_master; async. */
+int cbaa_mlp_to_bf16(const float *dev_master, uint16_t *dev_w_bf16, void *stream);
+
+/* Super-host decision per address, async: card = exp(ln(1 + est) + y) - 1
+ * with est the Thm. 2 estimate carried in the features, or est itself when
+ * y is not finite; decision = card >= theta.  dev_card float[n],
+ * dev_decision uint8[n]. */
+int cbaa_learned_decide(const float *dev_y, const float *dev_feats, size_t n, uint32_t log2_g, float theta,
+                        float *dev_card, uint8_t *dev_decision, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,13 @@ def _signatures():
         "cbaa_cube_update_multi": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                                   ctypes.POINTER(sz), vp, sz, vp]),
         "cbaa_set_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
+        "cbaa_host_features": (ctypes.c_int, [vp, vp, vp, vp, sz, vp, vp]),
+        "cbaa_mlp_forward": (ctypes.c_int, [vp, vp, sz, vp, vp]),
+        "cbaa_mlp_grad": (ctypes.c_int, [vp, vp, vp, sz, ctypes.c_float, vp, vp, vp]),
+        "cbaa_mlp_adam": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_uint32, vp]),
+        "cbaa_mlp_to_bf16": (ctypes.c_int, [vp, vp, vp]),
+        "cbaa_learned_decide": (ctypes.c_int, [vp, vp, sz, ctypes.c_uint32, ctypes.c_float, vp, vp, vp]),
         "cbaa_get_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
     }
 

@@ -8,6 +8,7 @@
 #include "cbaa_internal.cuh"
 #include "detect_layout.h"
 #include "update_binned.h"
+#include "learned.h"
 
 struct cbaa_cube {
     cbaa_params p;
@@ -320,6 +321,49 @@ int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_b
         if (cudaStreamSynchronize(s) != cudaSuccess) return CBAA_ERR_CUDA;
     }
     return info.n_hosts > cap ? CBAA_ERR_CAPACITY : CBAA_OK;
+}
+
+int cbaa_host_features(const cbaa_cube *cube, const uint64_t *dev_za, const double *dev_eps,
+                       const uint32_t *dev_ips, size_t n, float *dev_feats, void *stream) {
+    if (!cube || !dev_za || !dev_eps || (n && (!dev_ips || !dev_feats)) ||
+        (reinterpret_cast<uintptr_t>(dev_feats) & 15u))
+        return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_features(cube->G, cube->data, dev_za, dev_eps, dev_ips, n, dev_feats,
+                                             as_stream(stream)));
+}
+
+int cbaa_mlp_forward(const uint16_t *dev_w_bf16, const float *dev_x, size_t n, float *dev_y, void *stream) {
+    if (!dev_w_bf16 || (n && (!dev_x || !dev_y)) || (reinterpret_cast<uintptr_t>(dev_x) & 15u))
+        return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_mlp_forward(dev_w_bf16, dev_x, n, dev_y, as_stream(stream)));
+}
+
+int cbaa_mlp_grad(const uint16_t *dev_w_bf16, const float *dev_x, const float *dev_t, size_t n, float scale,
+                  float *dev_grad, float *dev_loss, void *stream) {
+    if (!dev_w_bf16 || !dev_grad || !dev_loss || (n && (!dev_x || !dev_t)) ||
+        (reinterpret_cast<uintptr_t>(dev_x) & 15u))
+        return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_mlp_grad(dev_w_bf16, dev_x, dev_t, n, scale, dev_grad, dev_loss,
+                                             as_stream(stream)));
+}
+
+int cbaa_mlp_adam(float *dev_master, const float *dev_grad, float *dev_m, float *dev_v, uint16_t *dev_w_bf16,
+                  float lr, float beta1, float beta2, float eps, uint32_t step, void *stream) {
+    if (!dev_master || !dev_grad || !dev_m || !dev_v || !dev_w_bf16 || step == 0) return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_adam(dev_master, dev_grad, dev_m, dev_v, dev_w_bf16, lr, beta1, beta2, eps, step,
+                                         as_stream(stream)));
+}
+
+int cbaa_mlp_to_bf16(const float *dev_master, uint16_t *dev_w_bf16, void *stream) {
+    if (!dev_master || !dev_w_bf16) return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_to_bf16(dev_master, dev_w_bf16, as_stream(stream)));
+}
+
+int cbaa_learned_decide(const float *dev_y, const float *dev_feats, size_t n, uint32_t log2_g, float theta,
+                        float *dev_card, uint8_t *dev_decision, void *stream) {
+    if ((n && (!dev_y || !dev_feats || !dev_card || !dev_decision)) || log2_g > 31) return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_decide(dev_y, dev_feats, n, (float)(1u << log2_g), theta, dev_card,
+                                           dev_decision, as_stream(stream)));
 }
 
 }  // extern "C"

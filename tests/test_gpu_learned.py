@@ -1,0 +1,150 @@
+"""Learned estimator: GPU features, forward and gradients against the CPU oracle, and its gain.
+
+The network's kernels are checked against oracle/mlp.py (fp64) at the same
+BF16 weights; the features against the oracle's cube arithmetic.  Then a
+network trained on one saturated window must estimate cardinalities on a
+held-out window better than Thm. 2 alone.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_1901_06207_b300 import traffic as T
+
+pytestmark = pytest.mark.gpu
+
+# Saturated regime: 16M-packet windows into a cube whose columns carry ~1.4 g
+# flows on average (4x fewer columns than the sizing rule asks for).
+THETA = 256
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1901_06207_b300 import build
+    build.build()
+    from paper_1901_06207_b300 import cbaa
+    return cbaa
+
+
+@pytest.fixture(scope="module")
+def geo(C):
+    return C.make_params(5, 3, 1, 8, [10])
+
+
+def _dev(a, dtype=None):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _window(seed):
+    return T.make_window(T.spec_window_64m(seed=seed, scale_shift=2))
+
+
+def test_features_match_oracle(C, oracle, geo):
+    from paper_1901_06207_b300 import learned as L
+    w = _window(0xC0FFEE44)
+    cube = C.Cube(geo)
+    cube.update_binned(_dev(w.pairs.view(np.int32)), C.UpdateWorkspace(geo, w.pairs.shape[0]))
+    host = oracle.build_cube(geo, w.pairs)
+    ips = np.concatenate([w.planted_ips[:50], w.pairs[:200, 0], np.array([1, 2, 0xFFFFFFFF], np.uint32)])
+    f = L.features(cube, THETA, _dev(ips.view(np.int32))).cpu().numpy()
+    zc, za = oracle.zero_counts(geo, host)
+    g = 1 << geo["log2_g"]
+    for k, ip in enumerate(ips.tolist()):
+        m = oracle.mangle(geo, ip)
+        cs, lp = m & ((1 << geo["r"]) - 1), m >> geo["r"]
+        cols = [oracle.ra_col(geo, i, lp) for i in range(3)] + [oracle.va_col(geo, 0, lp)]
+        for a in range(4):
+            assert f[k, a] == np.float32(zc[cs, a, cols[a]] / g)
+            assert abs(f[k, 5 + a] - za[cs, a] / ((1 << geo["cbn"][a]) * g)) < 1e-6
+        z = oracle.union_zeros(geo, host, ip)
+        e = oracle.eps(geo, za, cs)
+        assert f[k, 4] == np.float32(z / g) and abs(f[k, 9] - e) < 1e-6
+        est, _ = oracle.estimate(geo["log2_g"], z, e)
+        assert abs(f[k, 10] * g - est) <= 1e-5 * max(1.0, est)
+        assert f[k, 12] == (1.0 if z == 0 else 0.0)
+        ones = [max((g - zc[cs, a, cols[a]]) / g, 1 / g) for a in range(4)]
+        lu = math.log(max((g - z) / g, 1 / g))
+        assert abs(f[k, 15] - lu) < 1e-5 and abs(f[k, 14] - (lu - sum(math.log(o) for o in ones))) < 1e-4
+
+
+def _rand_net(C, seed):
+    from paper_1901_06207_b300 import learned as L
+    est = L.LearnedEstimator(seed=seed)
+    return est, M.bf16_to_f64(est.weights_bf16())
+
+
+def test_forward_matches_oracle(C):
+    est, w64 = _rand_net(C, 3)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(0, 1, (2000, 16)).astype(np.float32)
+    y = est.predict(_dev(X)).cpu().numpy()
+    want, _ = M.forward(w64, X)
+    assert np.allclose(y, want, rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("n", [1, 127, 3001])
+def test_gradient_matches_oracle(C, n):
+    """Kernel gradient (FP32 accumulation over tiles of 128, ragged tail) vs fp64 backpropagation."""
+    est, w64 = _rand_net(C, 5)
+    rng = np.random.default_rng(6)
+    X = rng.uniform(0, 1, (n, 16)).astype(np.float32)
+    t = rng.normal(2, 1, n).astype(np.float32)
+    loss, grad = est.loss_grad(_dev(X), _dev(t), scale=1.0 / n)
+    want_loss, want = M.loss_and_grad(w64, X, t, 1.0 / n)
+    got = grad.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - want_loss) <= 1e-4 * max(1.0, want_loss)
+    assert np.linalg.norm(got - want) <= 2e-4 * max(1e-6, np.linalg.norm(want))
+    big = np.abs(want) > 1e-3 * np.abs(want).max()
+    assert np.allclose(got[big], want[big], rtol=5e-3)
+
+
+def _dataset(C, oracle, geo, seed):
+    """What a deployed detector has: every address restored at the looser bound theta/2 (real hosts
+    and phantoms), its features, and -- for training and scoring -- its exact cardinality."""
+    import torch
+    from paper_1901_06207_b300 import learned as L
+    w = _window(seed)
+    cube = C.Cube(geo)
+    cube.update_binned(_dev(w.pairs.view(np.int32)), C.UpdateWorkspace(geo, w.pairs.shape[0]))
+    ips, cnt = oracle.exact_counts(w.pairs)
+    card = dict(zip(ips.tolist(), cnt.tolist()))
+    cand = cube.detect(THETA // 2)["ip"].astype(np.uint32)
+    truth = np.array([card.get(int(i), 0) for i in cand], dtype=np.float64)
+    X = L.features(cube, THETA, _dev(cand.view(np.int32)))
+    return X, truth, cand, cube, (ips, cnt)
+
+
+def test_training_beats_thm2_on_held_out_window(C, oracle, geo):
+    """Saturated cube: Thm. 2 lets thousands of phantoms through; the trained network rejects most."""
+    import torch
+    from paper_1901_06207_b300 import learned as L
+    Xtr, ttr, _, _, _ = _dataset(C, oracle, geo, 0xC0FFEE41)
+    Xte, tte, cte, cube, (ips, cnt) = _dataset(C, oracle, geo, 0xC0FFEE40)
+    net = L.LearnedEstimator(seed=7)
+    assert float(net.predict(Xte).abs().max().item()) == 0.0          # untrained: exactly Thm. 2
+    idx = torch.from_numpy(L.LearnedEstimator.balanced_indices(ttr)).cuda()
+    X = Xtr[idx].contiguous()
+    t = L.LearnedEstimator.target(X, torch.from_numpy(ttr.astype(np.float32)).cuda()[idx])
+    losses = net.train(X, t, epochs=40, batch=1 << 12, lr=3e-3)
+    assert losses[-1] < 0.5 * losses[0]
+    card, dec = net.decide(net.predict(Xte), Xte, geo["log2_g"], THETA)
+    dec = dec.cpu().numpy().astype(bool)
+    # Eq. 2 / Eq. 3 against the exact counts; plain = the method's host list at theta
+    fnr_p, fpr_p, nH = oracle.fnr_fpr(cube.detect(THETA)["ip"], ips, cnt, THETA)
+    fnr_l, fpr_l, _ = oracle.fnr_fpr(cte[dec], ips, cnt, THETA)
+    g = 1 << geo["log2_g"]
+    band = (tte >= THETA / 2) & (tte <= 4 * THETA)
+    card = card.cpu().numpy().astype(np.float64)
+    plain = Xte.cpu().numpy()[:, 10].astype(np.float64) * g
+    err_l = np.mean(np.abs(np.log1p(card[band]) - np.log1p(tte[band])))
+    err_p = np.mean(np.abs(np.log1p(plain[band]) - np.log1p(tte[band])))
+    print(f"held-out |H|={nH}: plain FNR {fnr_p:.4f} FPR {fpr_p:.4f} | learned FNR {fnr_l:.4f} FPR {fpr_l:.4f}"
+          f" | mean |ln err| on real hosts in [theta/2, 4 theta]: plain {err_p:.4f} learned {err_l:.4f}")
+    assert fpr_p > 1.0                          # the regime the network is for: phantoms swamp Thm. 2
+    assert fnr_l + fpr_l < 0.1 * (fnr_p + fpr_p)
+    assert fnr_l < 0.1
