@@ -266,8 +266,11 @@ def run_cbaa(args):
     cube = C.Cube(geo, device=dev)
     ws = C.Workspace(geo, max_candidates=1 << 18, device=dev)
     from paper_1901_06207_b300 import autotune
-    tuned = autotune.tune_update(geo, pairs_dev, device=dev, use_cache=False)
-    path = tuned["path"] if args.update == "auto" else args.update
+    if args.update == "auto":
+        tuned = autotune.tune_update(geo, pairs_dev, device=dev, use_cache=False)
+        path = tuned["path"]
+    else:
+        tuned, path = None, args.update            # library default shapes
     uws = C.UpdateWorkspace(geo, n, device=dev) if path == "binned" else None
     cap = 1 << 16
     out = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
@@ -380,8 +383,10 @@ def run_cbaa(args):
         "detect_ms": statistics.mean(det_ms), "detect_ms_p50": statistics.median(det_ms),
         "hosts_detected": int(inf["n_hosts"]), "hot_columns": int(inf["n_hot"]),
         "update_path": path,
-        "autotune": {"pick": tuned["path"], "tuning": tuned["tuning"], "best_ms": tuned["ms"],
-                     "worst_ms": tuned["worst_ms"], "candidates": tuned["candidates"]},
+        "autotune": None if tuned is None else {
+            "pick": tuned["path"], "tuning": tuned["tuning"], "best_ms": tuned["ms"],
+            "worst_ms": tuned["worst_ms"], "candidates": tuned["candidates"]},
+        "tuning": C.get_tuning(),
         "roofline": {"bound": "hbm", "kernel": f"update ({path}: " +
                      ("count+scan+scatter+apply" if uws is not None else "k_update") + ")",
                      "achieved": 8 * n / upd_s / 1e9, "peak": hbm_peak, "unit": "GB/s",

@@ -115,6 +115,11 @@ typedef struct cbaa_tuning {
     uint32_t count_blocks_per_sm;  /* partitioned update, counting kernel grid (default 8) */
     uint32_t apply_items_per_sm;   /* partitioned update, tile-assembly items per SM (default 8) */
     uint32_t direct_blocks_per_sm; /* direct update grid (default 8 blocks of 256 threads) */
+    uint32_t tile_kind;            /* partitioned update: 1 = column tiles (128 KiB runs of whole columns,
+                                      one routed code per bit), 2 = row tiles (one row word of every column
+                                      of a sketch, one routed record per packet; only where the geometry
+                                      allows: sketch words / W <= 32768 and tiles <= 8192), 0 = row tiles
+                                      where allowed, else column tiles */
 } cbaa_tuning;
 
 typedef struct cbaa_cube cbaa_cube;   /* opaque handle: a params copy plus the caller's memory */

@@ -168,16 +168,29 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(const Geo G, const 
     extern __shared__ uint32_t hist[];
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
     __syncthreads();
+    // four packets in flight per thread
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-        const uint32_t s = seg_of(S, p);
-        const uint32_t iip = ld_stream_u32(S.pairs[s] + 2 * (p - S.start[s]));
-        uint32_t t[NRA ? NRA + NVA : CBAA_MAX_ARRAYS];
-        const uint32_t A = source_tiles<NRA, NVA>(G, S.router[s] * S.seg_words, iip, t);
+    for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < n; p0 += 4 * stride) {
+        uint32_t iip[4], seg[4];
 #pragma unroll
-        for (uint32_t a = 0; a < (NRA ? NRA + NVA : CBAA_MAX_ARRAYS); ++a) {
-            if (NRA == 0 && a >= A) break;
-            atomicAdd(&hist[t[a]], 1u);
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t p = p0 + u * stride;
+            seg[u] = 0xFFFFFFFFu;
+            if (p < n) {
+                seg[u] = seg_of(S, p);
+                iip[u] = ld_stream_u32(S.pairs[seg[u]] + 2 * (p - S.start[seg[u]]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (seg[u] == 0xFFFFFFFFu) continue;
+            uint32_t t[NRA ? NRA + NVA : CBAA_MAX_ARRAYS];
+            const uint32_t A = source_tiles<NRA, NVA>(G, S.router[seg[u]] * S.seg_words, iip[u], t);
+#pragma unroll
+            for (uint32_t a = 0; a < (NRA ? NRA + NVA : CBAA_MAX_ARRAYS); ++a) {
+                if (NRA == 0 && a >= A) break;
+                atomicAdd(&hist[t[a]], 1u);
+            }
         }
     }
     __syncthreads();
@@ -199,7 +212,10 @@ __global__ void __launch_bounds__(1024) k_bin_scan(const uint32_t *__restrict__ 
     if (threadIdx.x == 0) offsets[nb] = total;
     __syncthreads();
     const uint32_t items = block_exclusive_scan(nchunk, item_start, nb, tmp);
-    if (threadIdx.x == 0) item_start[nb] = items;
+    if (threadIdx.x == 0) {
+        item_start[nb] = items;
+        nchunk[nb] = 0;                // queue counter of the row-tile apply
+    }
 }
 
 // THREADS x PPT packets per block.
@@ -418,9 +434,15 @@ cudaError_t launch_binned_t(const Geo &G, const BinSegs &S0, uint64_t n, const B
 
 }  // namespace
 
+cudaError_t launch_bin_scan(const uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s) {
+    k_bin_scan<<<1, 1024, 0, s>>>(counts, nb, ch, W.offsets, W.cursors, W.item_start, W.nchunk);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    if (T.tile_kind != 1 && rowtile_ok(G, S.n_routers)) return launch_update_rowtile(G, S, n, W, T, s);
     if (G.n_ra == 3 && G.n_va == 1) return launch_binned_t<3, 1>(G, S, n, W, T, s);
     return launch_binned_t<0, 0>(G, S, n, W, T, s);
 }

@@ -39,13 +39,29 @@ inline size_t bin_align(size_t x) { return (x + 255) / 256 * 256; }
 
 inline size_t bin_ws_fixed(uint32_t nb) { return 5 * bin_align(sizeof(uint32_t) * ((size_t)nb + 1)); }
 
+// Row tiles (update_rowtile.cu): one per (cube, sketch, row word), each
+// holding one word of every column of its sketch.
+constexpr uint32_t kMaxRowTiles = 8192;          // shared-memory tables of the routing kernel
+constexpr uint32_t kMaxRowTileWords = 32768;     // 128 KiB tile in shared memory
+inline uint32_t rowtile_bins_host(const Geo &G, uint32_t n_cubes) { return n_cubes * (G.smask + 1) * G.W; }
+inline bool rowtile_ok(const Geo &G, uint32_t n_cubes) {
+    return rowtile_bins_host(G, n_cubes) <= kMaxRowTiles && G.cs_words / G.W <= kMaxRowTileWords;
+}
+
+// Tables are sized for whichever tiling is used.
+inline uint32_t bin_ws_tables(const Geo &G, uint32_t n_cubes) {
+    const uint32_t col = n_cubes * tiles_per_cube(G);
+    const uint32_t row = rowtile_ok(G, n_cubes) ? rowtile_bins_host(G, n_cubes) : 0;
+    return col > row ? col : row;
+}
+
 inline size_t bin_ws_bytes(const Geo &G, uint32_t n_cubes, size_t max_pairs) {
-    return bin_ws_fixed(n_cubes * tiles_per_cube(G)) + bin_align(sizeof(uint32_t) * (size_t)G.A * max_pairs);
+    return bin_ws_fixed(bin_ws_tables(G, n_cubes)) + bin_align(sizeof(uint32_t) * (size_t)G.A * max_pairs);
 }
 
 // Carve `bytes` at `base` into a BinWs for n_cubes cubes; false if not even one packet fits.
 inline bool bin_ws_make(const Geo &G, uint32_t n_cubes, void *base, size_t bytes, BinWs *W) {
-    const uint32_t nb = n_cubes * tiles_per_cube(G);
+    const uint32_t nb = bin_ws_tables(G, n_cubes);
     const size_t fixed = bin_ws_fixed(nb);
     if (bytes < fixed + sizeof(uint32_t) * G.A) return false;
     size_t m = (bytes - fixed) / (sizeof(uint32_t) * G.A);
@@ -65,5 +81,8 @@ inline bool bin_ws_make(const Geo &G, uint32_t n_cubes, void *base, size_t bytes
 
 cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                                    cudaStream_t s);
+cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
+                                  cudaStream_t s);
+cudaError_t launch_bin_scan(const uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s);
 
 }  // namespace cbaa

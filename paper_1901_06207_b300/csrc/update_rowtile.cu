@@ -1,0 +1,346 @@
+// Alg. 1 by partition over row tiles: a third way to set the cube's bits,
+// with one routed record per packet instead of one per bit.
+//
+// A row tile is the pair (sketch cs, row word w): for every array a and
+// column col it holds the word w of column (cs, a, col) -- sum_a c_a words,
+// at most 128 KiB.  All |RA|+|VA| bits of a packet fall into the same row
+// tile (they share the sketch and the row, Alg. 1), so a packet is routed
+// once, as the 8-byte record {mangled iip, row | router << 16}; the tile
+// assembly recomputes its columns (the ring reads and the VA hash of
+// Alg. 1) and sets its bits with shared-memory atomics, then ORs every
+// non-zero word into the cube (the words of a row tile are one per column,
+// W words apart in the cube).
+//
+//   1. k_rt_count   : packets per row tile (one shared-memory atomic per packet)
+//   2. k_bin_scan   : (shared with the column-tile path) offsets and apply items
+//   3. k_rt_scatter : a block stages its packets' records grouped by row tile
+//                     and writes each run out coalesced
+//   4. k_rt_apply   : per item, assemble the row tile in shared memory, flush
+// Traffic per packet: 8 B read twice, an 8-byte record written and read once.
+#include <mutex>
+
+#include "cbaa_internal.cuh"
+#include "update_binned.h"
+
+namespace cbaa {
+
+cudaError_t launch_bin_scan(const uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s);
+
+namespace {
+
+constexpr uint32_t kCountThreads = 256;
+constexpr uint32_t kApplyThreads = 1024;
+
+__device__ __forceinline__ uint2 ld_pair(const uint32_t *p) {
+    uint2 v;
+    asm volatile("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_stream_v4(const uint4 *p) {
+    uint4 v;
+    asm volatile("ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_stream_v2(const uint2 *p) {
+    uint2 v;
+    asm volatile("ld.global.cs.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
+    asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t seg_of(const BinSegs &S, uint64_t p) {
+    uint32_t s = 0;
+    while (s + 1 < S.k && p >= S.start[s + 1]) ++s;
+    return s;
+}
+
+// Row tile of a packet: router r's tiles come first-to-last as (cs, w).
+__device__ __forceinline__ uint32_t row_tile(const Geo &G, uint32_t router, uint32_t m, uint32_t row) {
+    return (router * (G.smask + 1) + (m & G.smask)) * G.W + (row >> 5);
+}
+
+// Offset of (array a, column col) inside a row tile.
+__device__ __forceinline__ uint32_t tile_off(const Geo &G, uint32_t a, uint32_t col) {
+    return (G.arr_base[a] / G.W) + col;
+}
+
+__device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *tmp) {
+    const uint32_t T = blockDim.x, t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+    const uint32_t per = (n + T - 1) / T;
+    const uint32_t b0 = t * per < n ? t * per : n;
+    const uint32_t b1 = b0 + per < n ? b0 + per : n;
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i) s += in[i];
+    uint32_t x = s;
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < T / 32 ? tmp[lane] : 0u;
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        tmp[lane] = v;
+    }
+    __syncthreads();
+    uint32_t run = (warp ? tmp[warp - 1] : 0u) + x - s;
+    const uint32_t total = tmp[T / 32 - 1];
+    for (uint32_t i = b0; i < b1; ++i) {
+        const uint32_t v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
+                                                            uint32_t *__restrict__ counts) {
+    extern __shared__ uint32_t hist[];
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    // four packets in flight per thread
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < n; p0 += 4 * stride) {
+        uint2 v[4];
+        uint32_t seg[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t p = p0 + u * stride;
+            seg[u] = 0xFFFFFFFFu;
+            if (p < n) {
+                seg[u] = seg_of(S, p);
+                v[u] = ld_pair(S.pairs[seg[u]] + 2 * (p - S.start[seg[u]]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (seg[u] != 0xFFFFFFFFu)
+                atomicAdd(&hist[row_tile(G, S.router[seg[u]], mangle(G, v[u].x), row_of(G, v[u].y))], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
+        if (hist[i]) atomicAdd(&counts[i], hist[i]);
+}
+
+template <int THREADS, int PPT>
+__global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
+                                                        uint32_t *__restrict__ cursors, uint2 *__restrict__ recs) {
+    extern __shared__ uint32_t sm[];
+    uint32_t *hist = sm;
+    uint32_t *fill = sm + nb;
+    uint32_t *delta = sm + 2 * nb;
+    uint2 *staged = reinterpret_cast<uint2 *>(sm + ((3 * nb + 1) & ~1u));
+    uint32_t *sbin = reinterpret_cast<uint32_t *>(staged + THREADS * PPT);
+    __shared__ uint32_t tmp[32];
+    constexpr uint32_t P = THREADS * PPT;
+    const uint64_t p0 = (uint64_t)blockIdx.x * P;
+    const uint32_t np = (uint32_t)((n - p0) < P ? (n - p0) : P);
+
+    for (uint32_t i = threadIdx.x; i < nb; i += THREADS) hist[i] = 0;
+    __syncthreads();
+    uint2 rec[PPT];
+    uint32_t bin[PPT];
+#pragma unroll
+    for (uint32_t k = 0; k < PPT; ++k) {
+        const uint32_t p = threadIdx.x + k * THREADS;
+        bin[k] = 0xFFFFFFFFu;
+        if (p < np) {
+            const uint64_t gp = p0 + p;
+            const uint32_t s = seg_of(S, gp);
+            const uint2 v = ld_pair(S.pairs[s] + 2 * (gp - S.start[s]));
+            const uint32_t m = mangle(G, v.x), row = row_of(G, v.y);
+            rec[k] = make_uint2(m, row);
+            bin[k] = row_tile(G, S.router[s], m, row);
+            atomicAdd(&hist[bin[k]], 1u);
+        }
+    }
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan(hist, fill, nb, tmp);
+    for (uint32_t b = threadIdx.x; b < nb; b += THREADS) {
+        const uint32_t c = hist[b];
+        if (c) delta[b] = atomicAdd(&cursors[b], c) - fill[b];
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t k = 0; k < PPT; ++k) {
+        if (bin[k] != 0xFFFFFFFFu) {
+            const uint32_t pos = atomicAdd(&fill[bin[k]], 1u);
+            staged[pos] = rec[k];
+            sbin[pos] = bin[k];
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged[t];
+}
+
+// Items (a row tile's records, cut into chunks of ch only when a tile holds
+// more than ch) are taken from a queue, so blocks that drew small tiles take
+// more of them.
+__device__ __forceinline__ void rt_apply_rec(const Geo &G, uint32_t *tile, uint2 rv) {
+    const uint32_t lp = rv.x >> G.r;
+    const uint32_t bit = 1u << (rv.y & 31u);
+    for (uint32_t i = 0; i < G.n_ra; ++i) atomicOr(&tile[tile_off(G, i, ra_col(G, i, lp))], bit);
+    for (uint32_t j = 0; j < G.n_va; ++j) atomicOr(&tile[tile_off(G, G.n_ra + j, va_col(G, j, lp))], bit);
+}
+
+__global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const BinSegs S,
+                                                            const uint2 *__restrict__ recs,
+                                                            const uint32_t *__restrict__ offsets,
+                                                            const uint32_t *__restrict__ item_start, uint32_t nb,
+                                                            uint32_t ch, uint32_t tile_words,
+                                                            uint32_t *__restrict__ queue) {
+    extern __shared__ uint32_t tile[];
+    __shared__ uint32_t s_item;
+    const uint32_t items = item_start[nb];
+    const uint32_t tiles_per_router = (G.smask + 1) * G.W;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= items) break;
+        uint32_t lo = 0, hi = nb;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (item_start[mid] <= item) lo = mid; else hi = mid;
+        }
+        const uint32_t b = lo;
+        const uint32_t c0 = offsets[b] + (item - item_start[b]) * ch;
+        const uint32_t cend = offsets[b + 1];
+        const uint32_t c1 = c0 + ch < cend ? c0 + ch : cend;
+        for (uint32_t i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0;
+        __syncthreads();
+        uint32_t c = c0 + threadIdx.x;
+        for (; c + 3 * blockDim.x < c1; c += 4 * blockDim.x) {        // four records in flight
+            uint2 rv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rv[u] = ld_stream_v2(recs + c + u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rt_apply_rec(G, tile, rv[u]);
+        }
+        for (; c < c1; c += blockDim.x) rt_apply_rec(G, tile, ld_stream_v2(recs + c));
+        __syncthreads();
+        const uint32_t router = b / tiles_per_router;
+        const uint32_t rem = b - router * tiles_per_router;
+        const uint32_t cs = rem / G.W, w = rem - cs * G.W;
+        uint32_t *cube = S.cube[router] + (size_t)cs * G.cs_words + w;
+        for (uint32_t t = threadIdx.x; t < tile_words; t += blockDim.x) {
+            const uint32_t v = tile[t];
+            if (!v) continue;
+            uint32_t a = 0;                                   // array of tile word t
+            while (a + 1 < G.A && t >= G.arr_base[a + 1] / G.W) ++a;
+            const uint32_t col = t - G.arr_base[a] / G.W;
+            red_or(cube + G.arr_base[a] + (size_t)col * G.W, v);
+        }
+        __syncthreads();
+    }
+}
+
+std::mutex g_attr_mu;
+struct Grant { const void *fn; int dev; size_t bytes; };
+Grant g_grants[64];
+int g_ngrants = 0;
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const void *fn = reinterpret_cast<const void *>(kernel);
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    int i = 0;
+    for (; i < g_ngrants; ++i)
+        if (g_grants[i].fn == fn && g_grants[i].dev == dev) break;
+    if (i < g_ngrants && g_grants[i].bytes >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (i == g_ngrants) {
+        if (g_ngrants < 64) g_grants[g_ngrants++] = {fn, dev, bytes};
+    } else {
+        g_grants[i].bytes = bytes;
+    }
+    return cudaSuccess;
+}
+
+template <int THREADS, int PPT>
+cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
+                              cudaStream_t s) {
+    const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nb + 1) & ~(size_t)1) + 3ull * THREADS * PPT);
+    cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT>, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
+    k_rt_scatter<THREADS, PPT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors,
+                                                              reinterpret_cast<uint2 *>(W.codes));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t rowtile_bins(const Geo &G, uint32_t n_cubes) { return n_cubes * (G.smask + 1) * G.W; }
+uint32_t rowtile_words(const Geo &G) { return G.cs_words / G.W; }
+
+cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, const BinWs &W, const cbaa_tuning &T,
+                                  cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t nb = rowtile_bins(G, S0.n_routers);
+    const uint32_t tw = rowtile_words(G);
+    const int sms = num_sms();
+    const size_t apply_smem = sizeof(uint32_t) * tw;
+    cudaError_t e;
+    if ((e = allow_smem(k_rt_apply, apply_smem)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_rt_count, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
+    const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
+    const uint32_t apply_ips = T.apply_items_per_sm ? T.apply_items_per_sm : 8;
+    const uint64_t max_pairs = W.max_pairs * G.A / 2;       // records are 2 words, the buffer holds A per packet
+    for (uint64_t done = 0; done < n;) {
+        const uint64_t m = (n - done) < max_pairs ? (n - done) : max_pairs;
+        BinSegs S = S0;
+        S.k = 0;
+        for (uint32_t j = 0; j < S0.k; ++j) {
+            const uint64_t a = S0.start[j] > done ? S0.start[j] : done;
+            const uint64_t b = S0.start[j + 1] < done + m ? S0.start[j + 1] : done + m;
+            if (a >= b) continue;
+            S.pairs[S.k] = S0.pairs[j] + 2 * (a - S0.start[j]);
+            S.start[S.k] = a - done;
+            S.router[S.k] = S0.router[j];
+            ++S.k;
+        }
+        S.start[S.k] = m;
+        if ((e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * nb, s)) != cudaSuccess) return e;
+        const uint64_t want = (m + kCountThreads - 1) / kCountThreads;
+        const uint64_t cap = (uint64_t)sms * count_bps;
+        k_rt_count<<<(unsigned)(want < cap ? want : cap), kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb,
+                                                                                                 W.counts);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // split a row tile only when it holds more than apply_ips/2 times the average tile
+        uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
+        if (ch < (1u << 12)) ch = 1u << 12;
+        if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s)) != cudaSuccess) return e;
+        switch (T.scatter_shape) {
+            case 1: e = launch_rt_scatter<512, 4>(G, S, m, nb, W, s); break;
+            case 2: e = launch_rt_scatter<1024, 4>(G, S, m, nb, W, s); break;
+            case 3: e = launch_rt_scatter<256, 8>(G, S, m, nb, W, s); break;
+            case 4: e = launch_rt_scatter<256, 4>(G, S, m, nb, W, s); break;
+            default: e = launch_rt_scatter<512, 8>(G, S, m, nb, W, s); break;
+        }
+        if (e != cudaSuccess) return e;
+        k_rt_apply<<<(unsigned)sms, kApplyThreads, apply_smem, s>>>(G, S, reinterpret_cast<const uint2 *>(W.codes),
+                                                                    W.offsets, W.item_start, nb, (uint32_t)ch, tw,
+                                                                    W.nchunk + nb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        done += m;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace cbaa

@@ -105,14 +105,16 @@ def test_binned_update_passes_ragged_and_incremental(C, oracle):
     assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
+@pytest.mark.parametrize("kind", [1, 2])
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
-def test_binned_update_every_scatter_shape(C, oracle, shape):
-    """Launch shapes change timing only: every routing shape gives the oracle's cube."""
+def test_binned_update_every_scatter_shape(C, oracle, shape, kind):
+    """Launch shapes and tilings change timing only: every one gives the oracle's cube."""
     d = GEO.L2
     w = window("4m")
     before = C.get_tuning()
     try:
-        C.set_tuning(scatter_shape=shape, count_blocks_per_sm=2 + shape, apply_items_per_sm=1 + 3 * shape)
+        C.set_tuning(scatter_shape=shape, count_blocks_per_sm=2 + shape, apply_items_per_sm=1 + 3 * shape,
+                     tile_kind=kind)
         cube = C.Cube(d)
         cube.update_binned(dev_pairs(w.pairs), C.UpdateWorkspace(d, w.pairs.shape[0]))
         assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
@@ -120,9 +122,20 @@ def test_binned_update_every_scatter_shape(C, oracle, shape):
         C.set_tuning(**before)
 
 
-@pytest.mark.parametrize("geo,win,k", [("TINY2", "tiny", 5), ("L2", "4m", 8), ("TINY", "tiny", 16)])
-def test_multi_router_update(C, oracle, geo, win, k):
+@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("geo,win,k", [("TINY2", "tiny", 5), ("L2", "4m", 8), ("TINY", "tiny", 16),
+                                       ("PAPER", "1m", 2), ("SERVE", "4m", 1)])
+def test_multi_router_update(C, oracle, geo, win, k, kind):
     """One partitioned pass over k router cubes: each equals the oracle cube of its own packets."""
+    before = C.get_tuning()
+    C.set_tuning(**{**before, "tile_kind": kind})
+    try:
+        _multi_router_case(C, oracle, geo, win, k)
+    finally:
+        C.set_tuning(**before)
+
+
+def _multi_router_case(C, oracle, geo, win, k):
     d = GEO.ALL[geo]
     w = window(win)
     rid, _ = T.split_by_router(w.pairs, 91, k)
