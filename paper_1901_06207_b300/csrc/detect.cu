@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v) { return __reduce_add_s
 // than Zmax zero bits.  For i = 0 the hot columns become the seed tuples
 // (cs, hc_0) of the join; for i >= 1 they are stored key-major (key = low
 // |CP(i-1)| bits) with bucket offsets.
-__global__ void __launch_bounds__(256) k_hot_lists(const Geo G, WsPtrs P) {
+__global__ void __launch_bounds__(1024) k_hot_lists(const Geo G, WsPtrs P) {
     const uint32_t cs = blockIdx.x, i = blockIdx.y;
     const uint32_t ncol = 1u << G.cbn[i];
     const int64_t zm = P.zmax[cs];
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_hot_lists(const Geo G, WsPtrs P) {
     uint16_t *list = P.hc + ((size_t)cs * G.n_ra + i) * P.hc_stride;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 
-    __shared__ uint32_t warp_tot[8], warp_off[8], s_base, s_count;
+    __shared__ uint32_t warp_tot[32], warp_off[32], s_base, s_count;
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
 
@@ -212,9 +212,41 @@ __global__ void __launch_bounds__(256) k_join(const Geo G, const uint32_t *__res
     }
 }
 
+// Host lists of up to kRankMax entries are sorted by rank: every thread owns
+// one host and counts the hosts with a smaller ip (ties broken by index),
+// which is its place in the output; the keys are read tile by tile through
+// shared memory.  Longer lists go through the bitonic network in
+// k_sort_out.
+constexpr uint32_t kRankMax = 1u << 16;
+constexpr uint32_t kRankThreads = 64;
+constexpr uint32_t kRankTile = 4096;
+
+__global__ void __launch_bounds__(kRankThreads) k_rank_sort(WsPtrs P, cbaa_host *__restrict__ out, uint64_t cap) {
+    __shared__ uint32_t keys[kRankTile];
+    const uint32_t found = P.state->info.n_hosts;
+    const uint32_t n = found < P.m ? found : P.m;
+    if (n > kRankMax) return;
+    if ((uint64_t)blockIdx.x * kRankThreads >= n) return;
+    const uint32_t i = blockIdx.x * kRankThreads + threadIdx.x;
+    const uint32_t me = i < n ? P.hosts[i].ip : 0u;
+    uint32_t rank = 0;
+    for (uint32_t t0 = 0; t0 < n; t0 += kRankTile) {
+        const uint32_t len = (n - t0) < kRankTile ? (n - t0) : kRankTile;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < len; j += kRankThreads) keys[j] = P.hosts[t0 + j].ip;
+        __syncthreads();
+        for (uint32_t j = 0; j < len; ++j) {
+            const uint32_t k = keys[j];
+            rank += (k < me) || (k == me && t0 + j < i);
+        }
+    }
+    if (i < n && rank < cap) out[rank] = P.hosts[i];
+}
+
 // Sort the restored hosts by ip (bitonic network over (ip << 32 | index)
-// keys, in shared memory up to kSmemKeys keys, else in the workspace),
-// write the first min(n, cap) to `out`, and settle the status.
+// keys, in shared memory up to kSmemKeys keys, else in the workspace) when
+// the list is longer than k_rank_sort takes, write the first min(n, cap) to
+// `out`, and settle the status.
 constexpr uint32_t kSmemKeys = 4096;
 
 __global__ void __launch_bounds__(1024) k_sort_out(const Geo G, WsPtrs P, cbaa_host *__restrict__ out, uint64_t cap) {
@@ -224,6 +256,7 @@ __global__ void __launch_bounds__(1024) k_sort_out(const Geo G, WsPtrs P, cbaa_h
     const uint32_t n = found < P.m ? found : P.m;
     uint32_t N = 1;
     while (N < n) N <<= 1;
+    if (n <= kRankMax) N = 0;                     // sorted by k_rank_sort
     unsigned long long *keys = (N <= kSmemKeys) ? skeys : P.keys;
     for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
         keys[k] = (k < n) ? (((unsigned long long)P.hosts[k].ip << 32) | k) : ~0ull;
@@ -241,8 +274,9 @@ __global__ void __launch_bounds__(1024) k_sort_out(const Geo G, WsPtrs P, cbaa_h
         }
     }
     const uint64_t nw = n < cap ? n : cap;
-    for (uint32_t k = threadIdx.x; k < nw; k += blockDim.x)
-        out[k] = P.hosts[keys[k] & 0xFFFFFFFFull];
+    if (N)
+        for (uint32_t k = threadIdx.x; k < nw; k += blockDim.x)
+            out[k] = P.hosts[keys[k] & 0xFFFFFFFFull];
     if (threadIdx.x == 0) {
         uint32_t need = 0, tuples = 0;
         for (uint32_t s = 0; s + 1 < G.n_ra; ++s) {
@@ -276,7 +310,7 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
     if (e != cudaSuccess) return CBAA_ERR_CUDA;
     e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s);
     if (e != cudaSuccess) return CBAA_ERR_CUDA;
-    k_hot_lists<<<dim3(G.smask + 1, G.n_ra), 256, 0, s>>>(G, P);
+    k_hot_lists<<<dim3(G.smask + 1, G.n_ra), 1024, 0, s>>>(G, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
     const unsigned blocks = (unsigned)num_sms * 4;
     const uint32_t wpl = G.W >= 32 ? G.W / 32 : 1;
@@ -291,7 +325,12 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
         }
         if (e != cudaSuccess) return CBAA_ERR_CUDA;
     }
-    k_sort_out<<<1, 1024, 0, s>>>(G, P, out ? out : P.sorted, out ? cap : P.m);
+    cbaa_host *dst = out ? out : P.sorted;
+    const uint64_t dcap = out ? cap : P.m;
+    const uint64_t rank_n = P.m < kRankMax ? P.m : kRankMax;
+    k_rank_sort<<<(unsigned)((rank_n + kRankThreads - 1) / kRankThreads), kRankThreads, 0, s>>>(P, dst, dcap);
+    if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
+    k_sort_out<<<1, 1024, 0, s>>>(G, P, dst, dcap);
     if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
     if (info_copy) {
         e = cudaMemcpyAsync(info_copy, &P.state->info, sizeof(cbaa_detect_info), cudaMemcpyDeviceToDevice, s);

@@ -37,19 +37,6 @@ __device__ __forceinline__ uint2 ld_pair(const uint32_t *p) {
     return v;
 }
 
-__device__ __forceinline__ uint4 ld_stream_v4(const uint4 *p) {
-    uint4 v;
-    asm volatile("ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ uint2 ld_stream_v2(const uint2 *p) {
-    uint2 v;
-    asm volatile("ld.global.cs.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-    return v;
-}
-
 __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
     asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
@@ -150,18 +137,25 @@ __global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSe
     for (uint32_t i = threadIdx.x; i < nb; i += THREADS) hist[i] = 0;
     __syncthreads();
     uint2 rec[PPT];
-    uint32_t bin[PPT];
+    uint32_t bin[PPT], rt[PPT];
 #pragma unroll
-    for (uint32_t k = 0; k < PPT; ++k) {
+    for (uint32_t k = 0; k < PPT; ++k) {            // every load issued before any hashing
         const uint32_t p = threadIdx.x + k * THREADS;
         bin[k] = 0xFFFFFFFFu;
         if (p < np) {
             const uint64_t gp = p0 + p;
             const uint32_t s = seg_of(S, gp);
-            const uint2 v = ld_pair(S.pairs[s] + 2 * (gp - S.start[s]));
-            const uint32_t m = mangle(G, v.x), row = row_of(G, v.y);
+            rt[k] = S.router[s];
+            rec[k] = __ldg(reinterpret_cast<const uint2 *>(S.pairs[s] + 2 * (gp - S.start[s])));
+            bin[k] = 0;
+        }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < PPT; ++k) {
+        if (bin[k] != 0xFFFFFFFFu) {
+            const uint32_t m = mangle(G, rec[k].x), row = row_of(G, rec[k].y);
             rec[k] = make_uint2(m, row);
-            bin[k] = row_tile(G, S.router[s], m, row);
+            bin[k] = row_tile(G, rt[k], m, row);
             atomicAdd(&hist[bin[k]], 1u);
         }
     }
@@ -224,11 +218,11 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
         for (; c + 3 * blockDim.x < c1; c += 4 * blockDim.x) {        // four records in flight
             uint2 rv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) rv[u] = ld_stream_v2(recs + c + u * blockDim.x);
+            for (int u = 0; u < 4; ++u) rv[u] = __ldcs(recs + c + u * blockDim.x);
 #pragma unroll
             for (int u = 0; u < 4; ++u) rt_apply_rec(G, tile, rv[u]);
         }
-        for (; c < c1; c += blockDim.x) rt_apply_rec(G, tile, ld_stream_v2(recs + c));
+        for (; c < c1; c += blockDim.x) rt_apply_rec(G, tile, __ldcs(recs + c));
         __syncthreads();
         const uint32_t router = b / tiles_per_router;
         const uint32_t rem = b - router * tiles_per_router;
@@ -334,7 +328,11 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
             default: e = launch_rt_scatter<512, 8>(G, S, m, nb, W, s); break;
         }
         if (e != cudaSuccess) return e;
-        k_rt_apply<<<(unsigned)sms, kApplyThreads, apply_smem, s>>>(G, S, reinterpret_cast<const uint2 *>(W.codes),
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rt_apply, kApplyThreads, apply_smem) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        k_rt_apply<<<(unsigned)(sms * per_sm), kApplyThreads, apply_smem, s>>>(G, S, reinterpret_cast<const uint2 *>(W.codes),
                                                                     W.offsets, W.item_start, nb, (uint32_t)ch, tw,
                                                                     W.nchunk + nb);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
