@@ -452,6 +452,7 @@ def run_batched(args):
         b = np.concatenate([[0], np.cumsum(counts)])
         dev_w.append([p[b[j]:b[j + 1]] if counts[j] else None for j in range(R)])
     rw = RouterWindows(geo, R, theta, max_pairs=max(n_per), n_windows=len(wins), device=dev)
+    tiling = rw.tune(dev_w)
     rw.capture(dev_w)
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 1)):
@@ -506,7 +507,7 @@ def run_batched(args):
                        "step": "one CUDA graph replay: per window reset router cubes, one partitioned update "
                                "pass over all routers, OR-merge, detect",
                        "l2": "inputs larger than L2 (2 GiB of packets per step)"},
-            "window_ms": ms / steps / len(wins),
+            "window_ms": ms / steps / len(wins), "router_update_tiling": tiling,
             "plain_single_cube": {"value": plain_value, "unit": "Gpps", "window_ms": plain_ms / steps / len(wins),
                                   "path": "one cube, partitioned update of the whole window, detect, no graph"},
             "hosts_per_window": [int(i["n_hosts"]) for _, i in res],

@@ -46,6 +46,33 @@ class RouterWindows:
         for w, rp in enumerate(windows):
             self.enqueue_window(w, rp, stream)
 
+    def tune(self, windows, reps: int = 3):
+        """Pick the tiling of the partitioned update for these router cubes by timing the first window.
+
+        Sets the process-wide tuning; call before capture() so the graph records the choice."""
+        torch = C._torch()
+        stream = torch.cuda.current_stream()
+        best = None
+        base = C.get_tuning()
+        for kind in (1, 2):
+            C.set_tuning(**{**base, "tile_kind": kind})
+            times = []
+            for rep in range(reps + 1):
+                for c in self.routers:
+                    c.reset()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                C.update_multi(self.routers, windows[0], self.uws)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if rep:
+                    times.append(e0.elapsed_time(e1))
+            t = sorted(times)[len(times) // 2]
+            if best is None or t < best[1]:
+                best = (kind, t)
+        C.set_tuning(**{**base, "tile_kind": best[0]})
+        return {"tile_kind": best[0], "update_ms": best[1]}
+
     def capture(self, windows):
         """Record every window into one CUDA graph (after one eager pass on a side stream)."""
         torch = C._torch()

@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(256) k_join(const Geo G, const uint32_t *__res
 // shared memory.  Longer lists go through the bitonic network in
 // k_sort_out.
 constexpr uint32_t kRankMax = 1u << 16;
-constexpr uint32_t kRankThreads = 64;
+constexpr uint32_t kRankThreads = 256;
+constexpr uint32_t kRankLanes = 8;               // lanes sharing one host's count
 constexpr uint32_t kRankTile = 4096;
 
 __global__ void __launch_bounds__(kRankThreads) k_rank_sort(WsPtrs P, cbaa_host *__restrict__ out, uint64_t cap) {
@@ -226,8 +227,10 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_sort(WsPtrs P, cbaa_host 
     const uint32_t found = P.state->info.n_hosts;
     const uint32_t n = found < P.m ? found : P.m;
     if (n > kRankMax) return;
-    if ((uint64_t)blockIdx.x * kRankThreads >= n) return;
-    const uint32_t i = blockIdx.x * kRankThreads + threadIdx.x;
+    constexpr uint32_t per_block = kRankThreads / kRankLanes;
+    if ((uint64_t)blockIdx.x * per_block >= n) return;
+    const uint32_t sub = threadIdx.x % kRankLanes;
+    const uint32_t i = blockIdx.x * per_block + threadIdx.x / kRankLanes;
     const uint32_t me = i < n ? P.hosts[i].ip : 0u;
     uint32_t rank = 0;
     for (uint32_t t0 = 0; t0 < n; t0 += kRankTile) {
@@ -235,12 +238,21 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_sort(WsPtrs P, cbaa_host 
         __syncthreads();
         for (uint32_t j = threadIdx.x; j < len; j += kRankThreads) keys[j] = P.hosts[t0 + j].ip;
         __syncthreads();
-        for (uint32_t j = 0; j < len; ++j) {
-            const uint32_t k = keys[j];
-            rank += (k < me) || (k == me && t0 + j < i);
+        uint32_t r0 = 0, r1 = 0;
+        uint32_t j = sub;
+        for (; j + kRankLanes < len; j += 2 * kRankLanes) {
+            const uint32_t a = keys[j], b = keys[j + kRankLanes];
+            r0 += (a < me) || (a == me && t0 + j < i);
+            r1 += (b < me) || (b == me && t0 + j + kRankLanes < i);
         }
+        if (j < len) {
+            const uint32_t a = keys[j];
+            r0 += (a < me) || (a == me && t0 + j < i);
+        }
+        rank += r0 + r1;
     }
-    if (i < n && rank < cap) out[rank] = P.hosts[i];
+    for (uint32_t off = kRankLanes / 2; off > 0; off >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, off);
+    if (sub == 0 && i < n && rank < cap) out[rank] = P.hosts[i];
 }
 
 // Sort the restored hosts by ip (bitonic network over (ip << 32 | index)
@@ -328,7 +340,8 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
     cbaa_host *dst = out ? out : P.sorted;
     const uint64_t dcap = out ? cap : P.m;
     const uint64_t rank_n = P.m < kRankMax ? P.m : kRankMax;
-    k_rank_sort<<<(unsigned)((rank_n + kRankThreads - 1) / kRankThreads), kRankThreads, 0, s>>>(P, dst, dcap);
+    const uint64_t per_block = kRankThreads / kRankLanes;
+    k_rank_sort<<<(unsigned)((rank_n + per_block - 1) / per_block), kRankThreads, 0, s>>>(P, dst, dcap);
     if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
     k_sort_out<<<1, 1024, 0, s>>>(G, P, dst, dcap);
     if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;

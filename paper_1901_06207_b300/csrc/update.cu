@@ -129,21 +129,31 @@ __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t
     const uint4 *arr4 = reinterpret_cast<const uint4 *>(cube + (size_t)cs * G.cs_words + G.arr_base[a]);
 
     unsigned long long acc = 0;
-    for (uint32_t base = c0; base < c1; base += cols_per_iter) {
-        const uint32_t col = base + threadIdx.x / tpc;
-        uint32_t ones = 0;
-        if (col < c1) {
-            const uint4 *c4 = arr4 + (size_t)col * q;
-            for (uint32_t k = 0; k < per; ++k) {
-                const uint4 v = c4[sub + k * tpc];
-                ones += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    constexpr uint32_t U = 4;                        // columns in flight per thread group
+    for (uint32_t base = c0; base < c1; base += U * cols_per_iter) {
+        uint32_t ones[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) {
+            const uint32_t col = base + u * cols_per_iter + threadIdx.x / tpc;
+            ones[u] = 0;
+            if (col < c1) {
+                const uint4 *c4 = arr4 + (size_t)col * q;
+                for (uint32_t k = 0; k < per; ++k) {
+                    const uint4 v = c4[sub + k * tpc];
+                    ones[u] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                }
             }
         }
-        for (uint32_t off = tpc >> 1; off > 0; off >>= 1) ones += __shfl_xor_sync(0xffffffffu, ones, off);
-        if (col < c1 && sub == 0) {
-            const uint32_t zeros = G.g - ones;
-            if (zc) zc[(size_t)arr * G.cmax + col] = (uint16_t)zeros;
-            acc += zeros;
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) {
+            const uint32_t col = base + u * cols_per_iter + threadIdx.x / tpc;
+            uint32_t o = ones[u];
+            for (uint32_t off = tpc >> 1; off > 0; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+            if (col < c1 && sub == 0) {
+                const uint32_t zeros = G.g - o;
+                if (zc) zc[(size_t)arr * G.cmax + col] = (uint16_t)zeros;
+                acc += zeros;
+            }
         }
     }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
