@@ -42,6 +42,7 @@ Geo make_geo(const cbaa_params &p) {
         if ((1u << p.cbn[a]) > G.cmax) G.cmax = 1u << p.cbn[a];
     }
     G.arr_base[G.A] = base;
+    for (uint32_t a = 0; a <= G.A; ++a) G.col_base[a] = G.arr_base[a] / G.W;
     G.cs_words = base;
     G.cube_words = (uint64_t)base << p.r;
     for (uint32_t i = 0; i < G.n_ra; ++i) {

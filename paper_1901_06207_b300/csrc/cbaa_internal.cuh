@@ -25,6 +25,7 @@ struct Geo {
     uint32_t seed_m, seed_bv;
     uint32_t seed_va[CBAA_MAX_ARRAYS];
     uint32_t arr_base[CBAA_MAX_ARRAYS + 1];  // word offset of array a inside a CS
+    uint32_t col_base[CBAA_MAX_ARRAYS + 1];  // arr_base / W: first column of array a among a CS's columns
     uint32_t cs_words;                       // words of one CS
     uint64_t cube_words;
 };

@@ -54,7 +54,7 @@ __device__ __forceinline__ uint32_t row_tile(const Geo &G, uint32_t router, uint
 
 // Offset of (array a, column col) inside a row tile.
 __device__ __forceinline__ uint32_t tile_off(const Geo &G, uint32_t a, uint32_t col) {
-    return (G.arr_base[a] / G.W) + col;
+    return G.col_base[a] + col;
 }
 
 __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *tmp) {
@@ -181,13 +181,25 @@ __global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSe
 // Items (a row tile's records, cut into chunks of ch only when a tile holds
 // more than ch) are taken from a queue, so blocks that drew small tiles take
 // more of them.
+// NRA/NVA > 0 fix the array counts at compile time (the 3+1 layout); 0 reads them from G.
+template <int NRA, int NVA>
 __device__ __forceinline__ void rt_apply_rec(const Geo &G, uint32_t *tile, uint2 rv) {
+    const uint32_t nra = NRA ? NRA : G.n_ra, nva = NRA ? NVA : G.n_va;
     const uint32_t lp = rv.x >> G.r;
     const uint32_t bit = 1u << (rv.y & 31u);
-    for (uint32_t i = 0; i < G.n_ra; ++i) atomicOr(&tile[tile_off(G, i, ra_col(G, i, lp))], bit);
-    for (uint32_t j = 0; j < G.n_va; ++j) atomicOr(&tile[tile_off(G, G.n_ra + j, va_col(G, j, lp))], bit);
+#pragma unroll
+    for (uint32_t i = 0; i < (NRA ? NRA : CBAA_MAX_RA); ++i) {
+        if (NRA == 0 && i >= nra) break;
+        atomicOr(&tile[tile_off(G, i, ra_col(G, i, lp))], bit);
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < (NRA ? NVA : CBAA_MAX_ARRAYS); ++j) {
+        if (NRA == 0 && j >= nva) break;
+        atomicOr(&tile[tile_off(G, nra + j, va_col(G, j, lp))], bit);
+    }
 }
 
+template <int NRA, int NVA>
 __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const BinSegs S,
                                                             const uint2 *__restrict__ recs,
                                                             const uint32_t *__restrict__ offsets,
@@ -220,9 +232,9 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
 #pragma unroll
             for (int u = 0; u < 4; ++u) rv[u] = __ldcs(recs + c + u * blockDim.x);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) rt_apply_rec(G, tile, rv[u]);
+            for (int u = 0; u < 4; ++u) rt_apply_rec<NRA, NVA>(G, tile, rv[u]);
         }
-        for (; c < c1; c += blockDim.x) rt_apply_rec(G, tile, __ldcs(recs + c));
+        for (; c < c1; c += blockDim.x) rt_apply_rec<NRA, NVA>(G, tile, __ldcs(recs + c));
         __syncthreads();
         const uint32_t router = b / tiles_per_router;
         const uint32_t rem = b - router * tiles_per_router;
@@ -232,8 +244,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
             const uint32_t v = tile[t];
             if (!v) continue;
             uint32_t a = 0;                                   // array of tile word t
-            while (a + 1 < G.A && t >= G.arr_base[a + 1] / G.W) ++a;
-            const uint32_t col = t - G.arr_base[a] / G.W;
+            while (a + 1 < G.A && t >= G.col_base[a + 1]) ++a;
+            const uint32_t col = t - G.col_base[a];
             red_or(cube + G.arr_base[a] + (size_t)col * G.W, v);
         }
         __syncthreads();
@@ -281,7 +293,7 @@ cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32
 }  // namespace
 
 uint32_t rowtile_bins(const Geo &G, uint32_t n_cubes) { return n_cubes * (G.smask + 1) * G.W; }
-uint32_t rowtile_words(const Geo &G) { return G.cs_words / G.W; }
+uint32_t rowtile_words(const Geo &G) { return G.col_base[G.A]; }
 
 cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                                   cudaStream_t s) {
@@ -291,7 +303,8 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
     const int sms = num_sms();
     const size_t apply_smem = sizeof(uint32_t) * tw;
     cudaError_t e;
-    if ((e = allow_smem(k_rt_apply, apply_smem)) != cudaSuccess) return e;
+    const bool three_one = G.n_ra == 3 && G.n_va == 1;
+    if ((e = allow_smem(three_one ? k_rt_apply<3, 1> : k_rt_apply<0, 0>, apply_smem)) != cudaSuccess) return e;
     if ((e = allow_smem(k_rt_count, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
     const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
     const uint32_t apply_ips = T.apply_items_per_sm ? T.apply_items_per_sm : 8;
@@ -328,13 +341,13 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
             default: e = launch_rt_scatter<512, 8>(G, S, m, nb, W, s); break;
         }
         if (e != cudaSuccess) return e;
+        auto kapply = three_one ? k_rt_apply<3, 1> : k_rt_apply<0, 0>;
         int per_sm = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rt_apply, kApplyThreads, apply_smem) !=
-                cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kapply, kApplyThreads, apply_smem) != cudaSuccess ||
+            per_sm < 1)
             per_sm = 1;
-        k_rt_apply<<<(unsigned)(sms * per_sm), kApplyThreads, apply_smem, s>>>(G, S, reinterpret_cast<const uint2 *>(W.codes),
-                                                                    W.offsets, W.item_start, nb, (uint32_t)ch, tw,
-                                                                    W.nchunk + nb);
+        kapply<<<(unsigned)(sms * per_sm), kApplyThreads, apply_smem, s>>>(
+            G, S, reinterpret_cast<const uint2 *>(W.codes), W.offsets, W.item_start, nb, (uint32_t)ch, tw, W.nchunk + nb);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         done += m;
     }
