@@ -5,7 +5,8 @@
 // column col it holds the word w of column (cs, a, col) -- sum_a c_a words,
 // at most 128 KiB.  All |RA|+|VA| bits of a packet fall into the same row
 // tile (they share the sketch and the row, Alg. 1), so a packet is routed
-// once, as the 8-byte record {mangled iip, row | router << 16}; the tile
+// once, as a record {LP, bit position} (4 bytes when r >= 5, else the
+// 8 bytes {mangled iip, row}); the tile
 // assembly recomputes its columns (the ring reads and the VA hash of
 // Alg. 1) and sets its bits with shared-memory atomics, then ORs every
 // non-zero word into the cube (the words of a row tile are one per column,
@@ -16,7 +17,8 @@
 //   3. k_rt_scatter : a block stages its packets' records grouped by row tile
 //                     and writes each run out coalesced
 //   4. k_rt_apply   : per item, assemble the row tile in shared memory, flush
-// Traffic per packet: 8 B read twice, an 8-byte record written and read once.
+// Traffic per packet: 8 B read twice, a 4-byte (r >= 5) or 8-byte record
+// written and read once.
 #include <mutex>
 
 #include "cbaa_internal.cuh"
@@ -120,15 +122,17 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
         if (hist[i]) atomicAdd(&counts[i], hist[i]);
 }
 
-template <int THREADS, int PPT>
+// SHORT records (r >= 5): lp << 5 | bit in 4 bytes; else {mangled ip, row}.
+template <int THREADS, int PPT, bool SHORT>
 __global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
-                                                        uint32_t *__restrict__ cursors, uint2 *__restrict__ recs) {
+                                                        uint32_t *__restrict__ cursors, void *__restrict__ recs_out) {
     extern __shared__ uint32_t sm[];
     uint32_t *hist = sm;
     uint32_t *fill = sm + nb;
     uint32_t *delta = sm + 2 * nb;
     uint2 *staged = reinterpret_cast<uint2 *>(sm + ((3 * nb + 1) & ~1u));
-    uint32_t *sbin = reinterpret_cast<uint32_t *>(staged + THREADS * PPT);
+    uint32_t *staged1 = reinterpret_cast<uint32_t *>(staged);
+    uint32_t *sbin = SHORT ? staged1 + THREADS * PPT : reinterpret_cast<uint32_t *>(staged + THREADS * PPT);
     __shared__ uint32_t tmp[32];
     constexpr uint32_t P = THREADS * PPT;
     const uint64_t p0 = (uint64_t)blockIdx.x * P;
@@ -170,12 +174,19 @@ __global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSe
     for (uint32_t k = 0; k < PPT; ++k) {
         if (bin[k] != 0xFFFFFFFFu) {
             const uint32_t pos = atomicAdd(&fill[bin[k]], 1u);
-            staged[pos] = rec[k];
+            if (SHORT) staged1[pos] = ((rec[k].x >> G.r) << 5) | (rec[k].y & 31u);
+            else staged[pos] = rec[k];
             sbin[pos] = bin[k];
         }
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged[t];
+    if (SHORT) {
+        uint32_t *recs = static_cast<uint32_t *>(recs_out);
+        for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged1[t];
+    } else {
+        uint2 *recs = static_cast<uint2 *>(recs_out);
+        for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged[t];
+    }
 }
 
 // Items (a row tile's records, cut into chunks of ch only when a tile holds
@@ -183,10 +194,8 @@ __global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSe
 // more of them.
 // NRA/NVA > 0 fix the array counts at compile time (the 3+1 layout); 0 reads them from G.
 template <int NRA, int NVA>
-__device__ __forceinline__ void rt_apply_rec(const Geo &G, uint32_t *tile, uint2 rv) {
+__device__ __forceinline__ void rt_apply_lp(const Geo &G, uint32_t *tile, uint32_t lp, uint32_t bit) {
     const uint32_t nra = NRA ? NRA : G.n_ra, nva = NRA ? NVA : G.n_va;
-    const uint32_t lp = rv.x >> G.r;
-    const uint32_t bit = 1u << (rv.y & 31u);
 #pragma unroll
     for (uint32_t i = 0; i < (NRA ? NRA : CBAA_MAX_RA); ++i) {
         if (NRA == 0 && i >= nra) break;
@@ -200,8 +209,18 @@ __device__ __forceinline__ void rt_apply_rec(const Geo &G, uint32_t *tile, uint2
 }
 
 template <int NRA, int NVA>
+__device__ __forceinline__ void rt_apply_rec(const Geo &G, uint32_t *tile, uint2 rv) {
+    rt_apply_lp<NRA, NVA>(G, tile, rv.x >> G.r, 1u << (rv.y & 31u));
+}
+
+template <int NRA, int NVA>
+__device__ __forceinline__ void rt_apply_rec(const Geo &G, uint32_t *tile, uint32_t rv) {
+    rt_apply_lp<NRA, NVA>(G, tile, rv >> 5, 1u << (rv & 31u));
+}
+
+template <int NRA, int NVA, typename Rec>
 __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const BinSegs S,
-                                                            const uint2 *__restrict__ recs,
+                                                            const Rec *__restrict__ recs,
                                                             const uint32_t *__restrict__ offsets,
                                                             const uint32_t *__restrict__ item_start, uint32_t nb,
                                                             uint32_t ch, uint32_t tile_words,
@@ -228,7 +247,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
         __syncthreads();
         uint32_t c = c0 + threadIdx.x;
         for (; c + 3 * blockDim.x < c1; c += 4 * blockDim.x) {        // four records in flight
-            uint2 rv[4];
+            Rec rv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) rv[u] = __ldcs(recs + c + u * blockDim.x);
 #pragma unroll
@@ -278,15 +297,43 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaSuccess;
 }
 
-template <int THREADS, int PPT>
+template <int THREADS, int PPT, bool SHORT>
 cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                               cudaStream_t s) {
-    const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nb + 1) & ~(size_t)1) + 3ull * THREADS * PPT);
-    cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT>, smem);
+    const size_t per = SHORT ? 2 : 3;                 // staged record words + bin word per packet
+    const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nb + 1) & ~(size_t)1) + per * THREADS * PPT);
+    cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT, SHORT>, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
-    k_rt_scatter<THREADS, PPT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors,
-                                                              reinterpret_cast<uint2 *>(W.codes));
+    k_rt_scatter<THREADS, PPT, SHORT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes);
+    return cudaGetLastError();
+}
+
+template <bool SHORT>
+cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
+                                    uint32_t shape, cudaStream_t s) {
+    switch (shape) {
+        case 1: return launch_rt_scatter<512, 4, SHORT>(G, S, m, nb, W, s);
+        case 2: return launch_rt_scatter<1024, 4, SHORT>(G, S, m, nb, W, s);
+        case 3: return launch_rt_scatter<256, 8, SHORT>(G, S, m, nb, W, s);
+        case 4: return launch_rt_scatter<256, 4, SHORT>(G, S, m, nb, W, s);
+        default: return launch_rt_scatter<512, 8, SHORT>(G, S, m, nb, W, s);
+    }
+}
+
+template <typename Rec>
+cudaError_t launch_rt_apply(const Geo &G, const BinSegs &S, const BinWs &W, uint32_t nb, uint32_t ch, uint32_t tw,
+                            size_t smem, int sms, cudaStream_t s) {
+    const bool three_one = G.n_ra == 3 && G.n_va == 1;
+    auto kapply = three_one ? k_rt_apply<3, 1, Rec> : k_rt_apply<0, 0, Rec>;
+    cudaError_t e = allow_smem(kapply, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kapply, kApplyThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    kapply<<<(unsigned)(sms * per_sm), kApplyThreads, smem, s>>>(G, S, reinterpret_cast<const Rec *>(W.codes),
+                                                                 W.offsets, W.item_start, nb, ch, tw, W.nchunk + nb);
     return cudaGetLastError();
 }
 
@@ -303,12 +350,12 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
     const int sms = num_sms();
     const size_t apply_smem = sizeof(uint32_t) * tw;
     cudaError_t e;
-    const bool three_one = G.n_ra == 3 && G.n_va == 1;
-    if ((e = allow_smem(three_one ? k_rt_apply<3, 1> : k_rt_apply<0, 0>, apply_smem)) != cudaSuccess) return e;
     if ((e = allow_smem(k_rt_count, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
+    const bool short_rec = G.r >= 5;                  // lp (32 - r bits) and the bit fit one word
+    const uint64_t rec_words = short_rec ? 1 : 2;
     const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
     const uint32_t apply_ips = T.apply_items_per_sm ? T.apply_items_per_sm : 8;
-    const uint64_t max_pairs = W.max_pairs * G.A / 2;       // records are 2 words, the buffer holds A per packet
+    const uint64_t max_pairs = W.max_pairs * G.A / rec_words;   // the buffer holds A words per packet
     for (uint64_t done = 0; done < n;) {
         const uint64_t m = (n - done) < max_pairs ? (n - done) : max_pairs;
         BinSegs S = S0;
@@ -333,22 +380,12 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
         uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
         if (ch < (1u << 12)) ch = 1u << 12;
         if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s)) != cudaSuccess) return e;
-        switch (T.scatter_shape) {
-            case 1: e = launch_rt_scatter<512, 4>(G, S, m, nb, W, s); break;
-            case 2: e = launch_rt_scatter<1024, 4>(G, S, m, nb, W, s); break;
-            case 3: e = launch_rt_scatter<256, 8>(G, S, m, nb, W, s); break;
-            case 4: e = launch_rt_scatter<256, 4>(G, S, m, nb, W, s); break;
-            default: e = launch_rt_scatter<512, 8>(G, S, m, nb, W, s); break;
-        }
+        e = short_rec ? launch_rt_scatter_shape<true>(G, S, m, nb, W, T.scatter_shape, s)
+                      : launch_rt_scatter_shape<false>(G, S, m, nb, W, T.scatter_shape, s);
         if (e != cudaSuccess) return e;
-        auto kapply = three_one ? k_rt_apply<3, 1> : k_rt_apply<0, 0>;
-        int per_sm = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kapply, kApplyThreads, apply_smem) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-        kapply<<<(unsigned)(sms * per_sm), kApplyThreads, apply_smem, s>>>(
-            G, S, reinterpret_cast<const uint2 *>(W.codes), W.offsets, W.item_start, nb, (uint32_t)ch, tw, W.nchunk + nb);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s)
+                      : launch_rt_apply<uint2>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s);
+        if (e != cudaSuccess) return e;
         done += m;
     }
     return cudaSuccess;
