@@ -89,6 +89,17 @@ __host__ __device__ __forceinline__ uint32_t ra_col(const Geo &G, uint32_t i, ui
     return v & ((1u << G.cbn[i]) - 1u);
 }
 
+#ifdef __CUDACC__
+// Sets a bit of a shared-memory tile that only ever gains bits while it is
+// assembled.  A bit that a plain read already shows set stays set, so the
+// atomic is issued only for bits still clear: under duplicate packets and
+// heavy sources most sets land on set bits, and the read is far cheaper
+// than the shared-memory atomic.
+__device__ __forceinline__ void tile_set_bit(uint32_t *w, uint32_t bit) {
+    if (!(*reinterpret_cast<volatile uint32_t *>(w) & bit)) atomicOr(w, bit);
+}
+#endif
+
 __host__ __device__ __forceinline__ uint32_t col_word0(const Geo &G, uint32_t cs, uint32_t a, uint32_t col) {
     return cs * G.cs_words + G.arr_base[a] + col * G.W;
 }

@@ -63,7 +63,7 @@ __device__ __forceinline__ uint4 ld_stream_v4(const uint4 *p) {
 }
 
 __device__ __forceinline__ void apply_code(uint32_t *tile, uint32_t v) {
-    atomicOr(&tile[(v >> 5) & (kTileWords - 1u)], 1u << (v & 31u));
+    tile_set_bit(&tile[(v >> 5) & (kTileWords - 1u)], 1u << (v & 31u));
 }
 
 __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
@@ -382,6 +382,8 @@ cudaError_t launch_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uin
         case 2: return launch_scatter<NRA, NVA, 1024, 4>(G, S, m, nb, W, s);
         case 3: return launch_scatter<NRA, NVA, 256, 8>(G, S, m, nb, W, s);
         case 4: return launch_scatter<NRA, NVA, 256, 4>(G, S, m, nb, W, s);
+        case 5: return launch_scatter<NRA, NVA, 1024, 8>(G, S, m, nb, W, s);
+        case 6: return launch_scatter<NRA, NVA, 512, 16>(G, S, m, nb, W, s);
         default: return launch_scatter<NRA, NVA, 512, 8>(G, S, m, nb, W, s);
     }
 }

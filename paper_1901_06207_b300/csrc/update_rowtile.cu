@@ -93,29 +93,44 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
     return total;
 }
 
+__device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+// Blocks take tiles of kCountTile consecutive packets in turn.  A tile that
+// lies inside one segment at a 16-byte aligned address (the usual case) is
+// read as two 16-byte loads (two packets each) per thread with the segment
+// looked up once; any other tile packet by packet.
+constexpr uint32_t kCountTile = 4 * kCountThreads;
+
 __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                             uint32_t *__restrict__ counts) {
     extern __shared__ uint32_t hist[];
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    // four packets in flight per thread
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < n; p0 += 4 * stride) {
-        uint2 v[4];
-        uint32_t seg[4];
+    const uint32_t tiles_per_router = (G.smask + 1) * G.W;
+    for (uint64_t base = (uint64_t)blockIdx.x * kCountTile; base < n; base += (uint64_t)gridDim.x * kCountTile) {
+        const uint32_t s = seg_of(S, base);
+        const uint32_t *ptr = S.pairs[s] + 2 * (base - S.start[s]);
+        const bool fast = base + kCountTile <= S.start[s + 1] && (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0;
+        if (fast) {
+            const uint4 q0 = ld_quad(ptr + 4 * threadIdx.x);
+            const uint4 q1 = ld_quad(ptr + 4 * (threadIdx.x + kCountThreads));
+            const uint32_t rb = S.router[s] * tiles_per_router;
+            const uint32_t ip[4] = {q0.x, q0.z, q1.x, q1.z}, oip[4] = {q0.y, q0.w, q1.y, q1.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint64_t p = p0 + u * stride;
-            seg[u] = 0xFFFFFFFFu;
-            if (p < n) {
-                seg[u] = seg_of(S, p);
-                v[u] = ld_pair(S.pairs[seg[u]] + 2 * (p - S.start[seg[u]]));
+            for (int u = 0; u < 4; ++u)
+                atomicAdd(&hist[rb + row_tile(G, 0, mangle(G, ip[u]), row_of(G, oip[u]))], 1u);
+        } else {
+            const uint64_t end = base + kCountTile < n ? base + kCountTile : n;
+            for (uint64_t p = base + threadIdx.x; p < end; p += kCountThreads) {
+                const uint32_t sp = seg_of(S, p);
+                const uint2 v = ld_pair(S.pairs[sp] + 2 * (p - S.start[sp]));
+                atomicAdd(&hist[row_tile(G, S.router[sp], mangle(G, v.x), row_of(G, v.y))], 1u);
             }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (seg[u] != 0xFFFFFFFFu)
-                atomicAdd(&hist[row_tile(G, S.router[seg[u]], mangle(G, v[u].x), row_of(G, v[u].y))], 1u);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
@@ -128,7 +143,7 @@ __global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSe
                                                         uint32_t *__restrict__ cursors, void *__restrict__ recs_out) {
     extern __shared__ uint32_t sm[];
     uint32_t *hist = sm;
-    uint32_t *fill = sm + nb;
+    uint32_t *first = sm + nb;     // exclusive start of each tile's run in `staged`
     uint32_t *delta = sm + 2 * nb;
     uint2 *staged = reinterpret_cast<uint2 *>(sm + ((3 * nb + 1) & ~1u));
     uint32_t *staged1 = reinterpret_cast<uint32_t *>(staged);
@@ -141,42 +156,46 @@ __global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSe
     for (uint32_t i = threadIdx.x; i < nb; i += THREADS) hist[i] = 0;
     __syncthreads();
     uint2 rec[PPT];
-    uint32_t bin[PPT], rt[PPT];
+    uint32_t rt[PPT];
 #pragma unroll
     for (uint32_t k = 0; k < PPT; ++k) {            // every load issued before any hashing
         const uint32_t p = threadIdx.x + k * THREADS;
-        bin[k] = 0xFFFFFFFFu;
+        rt[k] = 0xFFFFFFFFu;
         if (p < np) {
             const uint64_t gp = p0 + p;
             const uint32_t s = seg_of(S, gp);
             rt[k] = S.router[s];
             rec[k] = __ldg(reinterpret_cast<const uint2 *>(S.pairs[s] + 2 * (gp - S.start[s])));
-            bin[k] = 0;
         }
     }
+    // per packet: its record and tile << 16 | its place in the tile's run (tiles < 2^16)
+    uint32_t slot[PPT];
 #pragma unroll
     for (uint32_t k = 0; k < PPT; ++k) {
-        if (bin[k] != 0xFFFFFFFFu) {
+        slot[k] = 0xFFFFFFFFu;
+        if (rt[k] != 0xFFFFFFFFu) {
             const uint32_t m = mangle(G, rec[k].x), row = row_of(G, rec[k].y);
-            rec[k] = make_uint2(m, row);
-            bin[k] = row_tile(G, rt[k], m, row);
-            atomicAdd(&hist[bin[k]], 1u);
+            const uint32_t b = row_tile(G, rt[k], m, row);
+            if (SHORT) rec[k].x = ((m >> G.r) << 5) | (row & 31u);
+            else rec[k] = make_uint2(m, row);
+            slot[k] = (b << 16) | atomicAdd(&hist[b], 1u);
         }
     }
     __syncthreads();
-    const uint32_t total = block_exclusive_scan(hist, fill, nb, tmp);
+    const uint32_t total = block_exclusive_scan(hist, first, nb, tmp);
     for (uint32_t b = threadIdx.x; b < nb; b += THREADS) {
         const uint32_t c = hist[b];
-        if (c) delta[b] = atomicAdd(&cursors[b], c) - fill[b];
+        if (c) delta[b] = atomicAdd(&cursors[b], c) - first[b];
     }
     __syncthreads();
 #pragma unroll
     for (uint32_t k = 0; k < PPT; ++k) {
-        if (bin[k] != 0xFFFFFFFFu) {
-            const uint32_t pos = atomicAdd(&fill[bin[k]], 1u);
-            if (SHORT) staged1[pos] = ((rec[k].x >> G.r) << 5) | (rec[k].y & 31u);
+        if (slot[k] != 0xFFFFFFFFu) {
+            const uint32_t b = slot[k] >> 16;
+            const uint32_t pos = first[b] + (slot[k] & 0xFFFFu);
+            if (SHORT) staged1[pos] = rec[k].x;
             else staged[pos] = rec[k];
-            sbin[pos] = bin[k];
+            sbin[pos] = b;
         }
     }
     __syncthreads();
@@ -199,12 +218,12 @@ __device__ __forceinline__ void rt_apply_lp(const Geo &G, uint32_t *tile, uint32
 #pragma unroll
     for (uint32_t i = 0; i < (NRA ? NRA : CBAA_MAX_RA); ++i) {
         if (NRA == 0 && i >= nra) break;
-        atomicOr(&tile[tile_off(G, i, ra_col(G, i, lp))], bit);
+        tile_set_bit(&tile[tile_off(G, i, ra_col(G, i, lp))], bit);
     }
 #pragma unroll
     for (uint32_t j = 0; j < (NRA ? NVA : CBAA_MAX_ARRAYS); ++j) {
         if (NRA == 0 && j >= nva) break;
-        atomicOr(&tile[tile_off(G, nra + j, va_col(G, j, lp))], bit);
+        tile_set_bit(&tile[tile_off(G, nra + j, va_col(G, j, lp))], bit);
     }
 }
 
@@ -317,6 +336,8 @@ cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, 
         case 2: return launch_rt_scatter<1024, 4, SHORT>(G, S, m, nb, W, s);
         case 3: return launch_rt_scatter<256, 8, SHORT>(G, S, m, nb, W, s);
         case 4: return launch_rt_scatter<256, 4, SHORT>(G, S, m, nb, W, s);
+        case 5: return launch_rt_scatter<1024, 8, SHORT>(G, S, m, nb, W, s);
+        case 6: return launch_rt_scatter<512, 16, SHORT>(G, S, m, nb, W, s);
         default: return launch_rt_scatter<512, 8, SHORT>(G, S, m, nb, W, s);
     }
 }
@@ -371,7 +392,7 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
         }
         S.start[S.k] = m;
         if ((e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * nb, s)) != cudaSuccess) return e;
-        const uint64_t want = (m + kCountThreads - 1) / kCountThreads;
+        const uint64_t want = (m + kCountTile - 1) / kCountTile;
         const uint64_t cap = (uint64_t)sms * count_bps;
         k_rt_count<<<(unsigned)(want < cap ? want : cap), kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb,
                                                                                                  W.counts);
