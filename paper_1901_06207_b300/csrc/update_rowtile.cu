@@ -138,8 +138,10 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
 }
 
 // SHORT records (r >= 5): lp << 5 | bit in 4 bytes; else {mangled ip, row}.
+// Shapes of up to 8 packets per thread are held to 32 registers (4-byte
+// records: 2048 threads per SM, measured ~8 % faster) or 42 (8-byte records).
 template <int THREADS, int PPT, bool SHORT>
-__global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
+__global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) / THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                         uint32_t *__restrict__ cursors, void *__restrict__ recs_out) {
     extern __shared__ uint32_t sm[];
     uint32_t *hist = sm;
@@ -157,15 +159,29 @@ __global__ void __launch_bounds__(THREADS) k_rt_scatter(const Geo G, const BinSe
     __syncthreads();
     uint2 rec[PPT];
     uint32_t rt[PPT];
+    // every load issued before any hashing; a block inside one segment at a
+    // 16-byte aligned address reads two packets per 16-byte load
+    const uint32_t s0 = seg_of(S, p0);
+    const uint32_t *ptr0 = S.pairs[s0] + 2 * (p0 - S.start[s0]);
+    if (np == P && p0 + P <= S.start[s0 + 1] && (reinterpret_cast<uintptr_t>(ptr0) & 15u) == 0) {
 #pragma unroll
-    for (uint32_t k = 0; k < PPT; ++k) {            // every load issued before any hashing
-        const uint32_t p = threadIdx.x + k * THREADS;
-        rt[k] = 0xFFFFFFFFu;
-        if (p < np) {
-            const uint64_t gp = p0 + p;
-            const uint32_t s = seg_of(S, gp);
-            rt[k] = S.router[s];
-            rec[k] = __ldg(reinterpret_cast<const uint2 *>(S.pairs[s] + 2 * (gp - S.start[s])));
+        for (uint32_t j = 0; j < PPT / 2; ++j) {
+            const uint4 q = ld_quad(ptr0 + 4 * (threadIdx.x + j * THREADS));
+            rec[2 * j] = make_uint2(q.x, q.y);
+            rec[2 * j + 1] = make_uint2(q.z, q.w);
+            rt[2 * j] = rt[2 * j + 1] = S.router[s0];
+        }
+    } else {
+#pragma unroll
+        for (uint32_t k = 0; k < PPT; ++k) {
+            const uint32_t p = threadIdx.x + k * THREADS;
+            rt[k] = 0xFFFFFFFFu;
+            if (p < np) {
+                const uint64_t gp = p0 + p;
+                const uint32_t s = seg_of(S, gp);
+                rt[k] = S.router[s];
+                rec[k] = __ldg(reinterpret_cast<const uint2 *>(S.pairs[s] + 2 * (gp - S.start[s])));
+            }
         }
     }
     // per packet: its record and tile << 16 | its place in the tile's run (tiles < 2^16)
