@@ -150,6 +150,29 @@ def _multi_router_case(C, oracle, geo, win, k):
     assert np.array_equal(glob.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
+@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("geo", ["L2", "PAPER"])
+def test_binned_update_skewed_runs(C, oracle, geo, kind):
+    """Half the packets one pair, a fifth one source to many peers: a few tiles take most of
+    the records (tile runs of millions next to runs of a few), against the oracle's cube."""
+    d = GEO.ALL[geo]
+    rng = np.random.default_rng(11)
+    n = 1_500_003
+    pairs = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    pairs[: n // 2] = (0x0A000001, 0x0B000002)
+    fan = slice(n // 2, n // 2 + n // 5)
+    pairs[fan, 0] = 0x0C000003
+    pairs = pairs[rng.permutation(n)]
+    before = C.get_tuning()
+    try:
+        C.set_tuning(**{**before, "tile_kind": kind})
+        cube = C.Cube(d)
+        cube.update_binned(dev_pairs(pairs), C.UpdateWorkspace(d, n))
+        assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, pairs))
+    finally:
+        C.set_tuning(**before)
+
+
 def test_update_ragged_and_unaligned(C, oracle):
     """Odd counts, a start that is only 8-byte aligned, empty and one-pair calls, uneven batches."""
     import torch
