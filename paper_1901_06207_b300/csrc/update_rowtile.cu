@@ -54,6 +54,32 @@ __device__ __forceinline__ uint32_t row_tile(const Geo &G, uint32_t router, uint
     return (router * (G.smask + 1) + (m & G.smask)) * G.W + (row >> 5);
 }
 
+// A block's own tile numbering.  Its packets lie in consecutive segments
+// [s_lo, s_lo + span); when span x (tiles per router) fits nb, tile t of
+// segment s is numbered (s - s_lo) x tpr + t, so a block that meets one or
+// two routers of many scans, zeroes and reserves only their tiles; otherwise
+// the global numbering router x tpr + t is kept.  unit(s) is the multiplier
+// of tpr for segment s in either case.
+struct BlockTiles {
+    uint32_t s_lo, nbl, tpr;
+    bool local;
+    __device__ uint32_t unit(const BinSegs &S, uint32_t s) const { return local ? s - s_lo : S.router[s]; }
+    __device__ uint32_t global(const BinSegs &S, uint32_t lb) const {
+        return local ? S.router[s_lo + lb / tpr] * tpr + lb % tpr : lb;
+    }
+};
+
+__device__ __forceinline__ BlockTiles block_tiles(const Geo &G, const BinSegs &S, uint64_t first, uint64_t last,
+                                                   uint32_t nb) {
+    BlockTiles B;
+    B.tpr = (G.smask + 1) * G.W;
+    B.s_lo = seg_of(S, first);
+    const uint32_t span = seg_of(S, last) - B.s_lo + 1;
+    B.local = (uint64_t)span * B.tpr <= nb;
+    B.nbl = B.local ? span * B.tpr : nb;
+    return B;
+}
+
 // Offset of (array a, column col) inside a row tile.
 __device__ __forceinline__ uint32_t tile_off(const Geo &G, uint32_t a, uint32_t col) {
     return G.col_base[a] + col;
@@ -99,48 +125,71 @@ __device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
     return v;
 }
 
-// Blocks take tiles of kCountTile consecutive packets in turn.  A tile that
-// lies inside one segment at a 16-byte aligned address (the usual case) is
-// read as two 16-byte loads (two packets each) per thread with the segment
-// looked up once; any other tile packet by packet.
+// MULTI (a pass over several cubes): block b counts the contiguous packets
+// [b chunk, (b+1) chunk), chunk a multiple of kCountTile, so that it meets
+// few segments and numbers only their tiles (BlockTiles).  Otherwise blocks
+// take tiles of kCountTile packets in turn.  A tile that lies inside one
+// segment at a 16-byte aligned address (the usual case) is read as two
+// 16-byte loads (two packets each) per thread with the segment looked up
+// once; any other tile packet by packet.
 constexpr uint32_t kCountTile = 4 * kCountThreads;
 
+template <bool MULTI>
 __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                             uint32_t *__restrict__ counts) {
     extern __shared__ uint32_t hist[];
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    uint64_t lo, hi, step;
+    if (MULTI) {
+        const uint64_t tiles = (n + kCountTile - 1) / kCountTile;
+        const uint64_t chunk = (tiles + gridDim.x - 1) / gridDim.x * kCountTile;
+        lo = (uint64_t)blockIdx.x * chunk;
+        if (lo >= n) return;                               // the whole block leaves before any barrier
+        hi = lo + chunk < n ? lo + chunk : n;
+        step = kCountTile;
+    } else {
+        lo = (uint64_t)blockIdx.x * kCountTile;
+        hi = n;
+        step = (uint64_t)gridDim.x * kCountTile;
+    }
+    BlockTiles B;
+    if (MULTI) {
+        B = block_tiles(G, S, lo, hi - 1, nb);
+    } else {
+        B.s_lo = 0; B.nbl = nb; B.tpr = (G.smask + 1) * G.W; B.local = false;
+    }
+    for (uint32_t i = threadIdx.x; i < B.nbl; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    const uint32_t tiles_per_router = (G.smask + 1) * G.W;
-    for (uint64_t base = (uint64_t)blockIdx.x * kCountTile; base < n; base += (uint64_t)gridDim.x * kCountTile) {
+    for (uint64_t base = lo; base < hi; base += step) {
         const uint32_t s = seg_of(S, base);
         const uint32_t *ptr = S.pairs[s] + 2 * (base - S.start[s]);
-        const bool fast = base + kCountTile <= S.start[s + 1] && (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0;
+        const bool fast = base + kCountTile <= hi && base + kCountTile <= S.start[s + 1] &&
+                          (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0;
         if (fast) {
             const uint4 q0 = ld_quad(ptr + 4 * threadIdx.x);
             const uint4 q1 = ld_quad(ptr + 4 * (threadIdx.x + kCountThreads));
-            const uint32_t rb = S.router[s] * tiles_per_router;
+            const uint32_t rb = B.unit(S, s) * B.tpr;
             const uint32_t ip[4] = {q0.x, q0.z, q1.x, q1.z}, oip[4] = {q0.y, q0.w, q1.y, q1.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 atomicAdd(&hist[rb + row_tile(G, 0, mangle(G, ip[u]), row_of(G, oip[u]))], 1u);
         } else {
-            const uint64_t end = base + kCountTile < n ? base + kCountTile : n;
+            const uint64_t end = base + kCountTile < hi ? base + kCountTile : hi;
             for (uint64_t p = base + threadIdx.x; p < end; p += kCountThreads) {
                 const uint32_t sp = seg_of(S, p);
                 const uint2 v = ld_pair(S.pairs[sp] + 2 * (p - S.start[sp]));
-                atomicAdd(&hist[row_tile(G, S.router[sp], mangle(G, v.x), row_of(G, v.y))], 1u);
+                atomicAdd(&hist[row_tile(G, B.unit(S, sp), mangle(G, v.x), row_of(G, v.y))], 1u);
             }
         }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
-        if (hist[i]) atomicAdd(&counts[i], hist[i]);
+    for (uint32_t i = threadIdx.x; i < B.nbl; i += blockDim.x)
+        if (hist[i]) atomicAdd(&counts[B.global(S, i)], hist[i]);
 }
 
 // SHORT records (r >= 5): lp << 5 | bit in 4 bytes; else {mangled ip, row}.
 // Shapes of up to 8 packets per thread are held to 32 registers (4-byte
 // records: 2048 threads per SM, measured ~8 % faster) or 42 (8-byte records).
-template <int THREADS, int PPT, bool SHORT>
+template <int THREADS, int PPT, bool SHORT, bool MULTI>
 __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) / THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                         uint32_t *__restrict__ cursors, void *__restrict__ recs_out) {
     extern __shared__ uint32_t sm[];
@@ -154,11 +203,18 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     constexpr uint32_t P = THREADS * PPT;
     const uint64_t p0 = (uint64_t)blockIdx.x * P;
     const uint32_t np = (uint32_t)((n - p0) < P ? (n - p0) : P);
-
-    for (uint32_t i = threadIdx.x; i < nb; i += THREADS) hist[i] = 0;
+    __shared__ BlockTiles sB;                         // MULTI: kept in shared memory, registers are short here
+    if (MULTI) {
+        if (threadIdx.x == 0) sB = block_tiles(G, S, p0, p0 + np - 1, nb);
+        __syncthreads();
+    }
+    BlockTiles one;                                   // one cube: the global numbering, folded at compile time
+    one.s_lo = 0; one.nbl = nb; one.tpr = (G.smask + 1) * G.W; one.local = false;
+    const BlockTiles &B = MULTI ? sB : one;
+    for (uint32_t i = threadIdx.x; i < B.nbl; i += THREADS) hist[i] = 0;
     __syncthreads();
     uint2 rec[PPT];
-    uint32_t rt[PPT];
+    uint32_t rt[PPT];                                 // the packet's unit (BlockTiles), or none
     // every load issued before any hashing; a block inside one segment at a
     // 16-byte aligned address reads two packets per 16-byte load
     const uint32_t s0 = seg_of(S, p0);
@@ -169,7 +225,7 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
             const uint4 q = ld_quad(ptr0 + 4 * (threadIdx.x + j * THREADS));
             rec[2 * j] = make_uint2(q.x, q.y);
             rec[2 * j + 1] = make_uint2(q.z, q.w);
-            rt[2 * j] = rt[2 * j + 1] = S.router[s0];
+            rt[2 * j] = rt[2 * j + 1] = B.unit(S, s0);
         }
     } else {
 #pragma unroll
@@ -179,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
             if (p < np) {
                 const uint64_t gp = p0 + p;
                 const uint32_t s = seg_of(S, gp);
-                rt[k] = S.router[s];
+                rt[k] = B.unit(S, s);
                 rec[k] = __ldg(reinterpret_cast<const uint2 *>(S.pairs[s] + 2 * (gp - S.start[s])));
             }
         }
@@ -198,10 +254,10 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
         }
     }
     __syncthreads();
-    const uint32_t total = block_exclusive_scan(hist, first, nb, tmp);
-    for (uint32_t b = threadIdx.x; b < nb; b += THREADS) {
+    const uint32_t total = block_exclusive_scan(hist, first, B.nbl, tmp);
+    for (uint32_t b = threadIdx.x; b < B.nbl; b += THREADS) {
         const uint32_t c = hist[b];
-        if (c) delta[b] = atomicAdd(&cursors[b], c) - first[b];
+        if (c) delta[b] = atomicAdd(&cursors[B.global(S, b)], c) - first[b];
     }
     __syncthreads();
 #pragma unroll
@@ -332,29 +388,29 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaSuccess;
 }
 
-template <int THREADS, int PPT, bool SHORT>
+template <int THREADS, int PPT, bool SHORT, bool MULTI>
 cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                               cudaStream_t s) {
     const size_t per = SHORT ? 2 : 3;                 // staged record words + bin word per packet
     const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nb + 1) & ~(size_t)1) + per * THREADS * PPT);
-    cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT, SHORT>, smem);
+    cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT, SHORT, MULTI>, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
-    k_rt_scatter<THREADS, PPT, SHORT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes);
+    k_rt_scatter<THREADS, PPT, SHORT, MULTI><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes);
     return cudaGetLastError();
 }
 
-template <bool SHORT>
+template <bool SHORT, bool MULTI>
 cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                                     uint32_t shape, cudaStream_t s) {
     switch (shape) {
-        case 1: return launch_rt_scatter<512, 4, SHORT>(G, S, m, nb, W, s);
-        case 2: return launch_rt_scatter<1024, 4, SHORT>(G, S, m, nb, W, s);
-        case 3: return launch_rt_scatter<256, 8, SHORT>(G, S, m, nb, W, s);
-        case 4: return launch_rt_scatter<256, 4, SHORT>(G, S, m, nb, W, s);
-        case 5: return launch_rt_scatter<1024, 8, SHORT>(G, S, m, nb, W, s);
-        case 6: return launch_rt_scatter<512, 16, SHORT>(G, S, m, nb, W, s);
-        default: return launch_rt_scatter<512, 8, SHORT>(G, S, m, nb, W, s);
+        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI>(G, S, m, nb, W, s);
+        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI>(G, S, m, nb, W, s);
+        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI>(G, S, m, nb, W, s);
+        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI>(G, S, m, nb, W, s);
+        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI>(G, S, m, nb, W, s);
+        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI>(G, S, m, nb, W, s);
+        default: return launch_rt_scatter<512, 8, SHORT, MULTI>(G, S, m, nb, W, s);
     }
 }
 
@@ -387,7 +443,9 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
     const int sms = num_sms();
     const size_t apply_smem = sizeof(uint32_t) * tw;
     cudaError_t e;
-    if ((e = allow_smem(k_rt_count, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
+    const bool multi = S0.n_routers > 1;
+    if ((e = allow_smem(multi ? k_rt_count<true> : k_rt_count<false>, sizeof(uint32_t) * nb)) != cudaSuccess)
+        return e;
     const bool short_rec = G.r >= 5;                  // lp (32 - r bits) and the bit fit one word
     const uint64_t rec_words = short_rec ? 1 : 2;
     const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
@@ -410,15 +468,20 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
         if ((e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * nb, s)) != cudaSuccess) return e;
         const uint64_t want = (m + kCountTile - 1) / kCountTile;
         const uint64_t cap = (uint64_t)sms * count_bps;
-        k_rt_count<<<(unsigned)(want < cap ? want : cap), kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb,
-                                                                                                 W.counts);
+        const unsigned cgrid = (unsigned)(want < cap ? want : cap);
+        if (multi) k_rt_count<true><<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts);
+        else k_rt_count<false><<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // split a row tile only when it holds more than apply_ips/2 times the average tile
         uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
         if (ch < (1u << 12)) ch = 1u << 12;
         if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s)) != cudaSuccess) return e;
-        e = short_rec ? launch_rt_scatter_shape<true>(G, S, m, nb, W, T.scatter_shape, s)
-                      : launch_rt_scatter_shape<false>(G, S, m, nb, W, T.scatter_shape, s);
+        if (multi)
+            e = short_rec ? launch_rt_scatter_shape<true, true>(G, S, m, nb, W, T.scatter_shape, s)
+                          : launch_rt_scatter_shape<false, true>(G, S, m, nb, W, T.scatter_shape, s);
+        else
+            e = short_rec ? launch_rt_scatter_shape<true, false>(G, S, m, nb, W, T.scatter_shape, s)
+                          : launch_rt_scatter_shape<false, false>(G, S, m, nb, W, T.scatter_shape, s);
         if (e != cudaSuccess) return e;
         e = short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s)
                       : launch_rt_apply<uint2>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s);
