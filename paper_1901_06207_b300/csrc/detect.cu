@@ -17,6 +17,7 @@
 // registers (g/32 words spread over 32 lanes), so no union-column buffer
 // pool is needed.
 #include <cmath>
+#include <cstddef>
 
 #include "cbaa_internal.cuh"
 #include "detect_layout.h"
@@ -26,6 +27,10 @@ namespace cbaa {
 namespace {
 
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) { return __reduce_add_sync(0xffffffffu, v); }
+
+static_assert(sizeof(cbaa_host) == 16 && offsetof(cbaa_host, z_union) == 4 && offsetof(cbaa_host, est) == 8 &&
+                  offsetof(cbaa_host, flags) == 12,
+              "the join stages hosts as 16-byte {ip, z_union, est, flags} records");
 
 // ---------------------------------------------------------------------------
 // Alg. 2.  Block (cs, i) lists the columns of RA i of sketch cs with no more
@@ -134,6 +139,24 @@ __global__ void __launch_bounds__(256) k_join(const Geo G, const uint32_t *__res
     const Tuple *__restrict__ in = P.tup[(s - 1) & 1];
     Tuple *__restrict__ out = P.tup[s & 1];
     const bool lane_live = (WPL > 1) || lane < G.W;
+    // Each warp stages its outputs (tuples, or hosts in the last stage; both
+    // 16-byte records) and reserves their slots with one atomic per 32, not
+    // one per output: thousands of outputs would otherwise queue on one
+    // counter.
+    __shared__ uint4 wbuf[8][32];
+    uint4 *mybuf = wbuf[threadIdx.x >> 5];
+    uint32_t *counter = last ? &P.state->info.n_hosts : &P.state->stage_count[s];
+    uint4 *dst = last ? reinterpret_cast<uint4 *>(P.hosts) : reinterpret_cast<uint4 *>(out);
+    uint32_t nbuf = 0;                                 // the same in every lane
+    auto flush = [&]() {
+        __syncwarp();
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(counter, nbuf);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane < nbuf && base + lane < P.m) dst[base + lane] = mybuf[lane];
+        nbuf = 0;
+        __syncwarp();
+    };
 
     for (uint32_t t = gw; t < n_in; t += nw) {
         const Tuple tu = in[t];
@@ -158,58 +181,82 @@ __global__ void __launch_bounds__(256) k_join(const Geo G, const uint32_t *__res
             for (uint32_t i = 0; i < s; ++i) lp_part |= ((uint32_t)tu.hc[i] & ((1u << G.ep[i]) - 1u)) << G.ring_off[i];
         const uint32_t close_bits = (uint32_t)tu.hc[0] & ((1u << G.cp[s]) - 1u);
 
-        for (uint32_t e = b0; e < b1; ++e) {
-            const uint32_t col = list[e];
-            if (last && (col >> G.ep[s]) != close_bits) continue;     // ring closure (Alg. 3 step 1)
-            uint32_t v[WPL];
-            load_col<WPL>(cube + col_word0(G, cs, s, col), G.W, lane, v);
+        // U candidates per iteration: their list entries, then all their column
+        // loads (and, in the last stage, the VA columns, which need only the
+        // list entry), then the U reductions.  ok[u] is the same in every lane.
+        constexpr int U = WPL >= 4 ? 1 : 4 / WPL;
+        for (uint32_t e0 = b0; e0 < b1; e0 += U) {
+            uint32_t col[U];
+            bool ok[U];
 #pragma unroll
-            for (int k = 0; k < WPL; ++k) v[k] &= acc[k];
-            uint32_t lp = 0;
+            for (int u = 0; u < U; ++u) {
+                ok[u] = e0 + u < b1;
+                col[u] = ok[u] ? (uint32_t)list[e0 + u] : 0u;
+                if (last && ok[u] && (col[u] >> G.ep[s]) != close_bits) ok[u] = false;   // ring closure (Alg. 3 step 1)
+            }
+            uint32_t v[U][WPL], lp[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (ok[u]) {
+                    load_col<WPL>(cube + col_word0(G, cs, s, col[u]), G.W, lane, v[u]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < WPL; ++k) v[u][k] = 0u;
+                }
+                lp[u] = lp_part | ((col[u] & ((1u << G.ep[s]) - 1u)) << G.ring_off[s]);   // step 2
+            }
             if (last) {
-                lp = lp_part | ((col & ((1u << G.ep[s]) - 1u)) << G.ring_off[s]);   // step 2
-                for (uint32_t j = 0; j < G.n_va; ++j) {                               // step 3
-                    uint32_t w[WPL];
-                    load_col<WPL>(cube + col_word0(G, cs, G.n_ra + j, va_col(G, j, lp)), G.W, lane, w);
+                for (uint32_t j = 0; j < G.n_va; ++j) {                                     // step 3
+                    uint32_t w[U][WPL];
 #pragma unroll
-                    for (int k = 0; k < WPL; ++k) v[k] &= w[k];
+                    for (int u = 0; u < U; ++u) {
+                        if (ok[u]) {
+                            load_col<WPL>(cube + col_word0(G, cs, G.n_ra + j, va_col(G, j, lp[u])), G.W, lane, w[u]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < WPL; ++k) w[u][k] = 0u;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int k = 0; k < WPL; ++k) v[u][k] &= w[u][k];
                 }
             }
-            uint32_t ones = 0;
-            if (lane_live) {
 #pragma unroll
-                for (int k = 0; k < WPL; ++k) ones += __popc(v[k]);
-            }
-            ones = warp_sum(ones);
-            const uint32_t zeros = G.g - ones;
-            if ((int64_t)zeros > zm || lane != 0) continue;                     // step 4
-            if (!last) {
-                const uint32_t slot = atomicAdd(&P.state->stage_count[s], 1u);
-                if (slot < P.m) {
-                    Tuple o = tu;
-                    o.hc[s] = (uint16_t)col;
-                    out[slot] = o;
+            for (int u = 0; u < U; ++u) {
+                if (!ok[u]) continue;
+                uint32_t ones = 0;
+                if (lane_live) {
+#pragma unroll
+                    for (int k = 0; k < WPL; ++k) ones += __popc(v[u][k] & acc[k]);
                 }
-            } else {
-                const uint32_t slot = atomicAdd(&P.state->info.n_hosts, 1u);
-                if (slot < P.m) {
-                    // Thm. 2 estimate; Z = 0 is reported with Z = 1 and flagged.
-                    const double g = (double)G.g;
-                    const double eps = P.eps[cs];
-                    const uint32_t zs = zeros ? zeros : 1u;
-                    const double den = __dsub_rn(g, __dmul_rn(g, eps));
-                    double est = __dmul_rn(-g, log(__ddiv_rn((double)zs, den)));
-                    if (est < 0.0) est = 0.0;
-                    cbaa_host h;
-                    h.ip = unmangle(G, (lp << G.r) | cs);
-                    h.z_union = zeros;
-                    h.est = (float)est;
-                    h.flags = zeros ? 0u : CBAA_FLAG_SATURATED;
-                    P.hosts[slot] = h;
+                ones = warp_sum(ones);
+                const uint32_t zeros = G.g - ones;
+                if ((int64_t)zeros > zm) continue;                                   // step 4
+                if (lane == 0) {
+                    if (!last) {
+                        Tuple o = tu;
+                        o.hc[s] = (uint16_t)col[u];
+                        mybuf[nbuf] = *reinterpret_cast<const uint4 *>(&o);
+                    } else {
+                        // Thm. 2 estimate; Z = 0 is reported with Z = 1 and flagged.
+                        const double g = (double)G.g;
+                        const double eps = P.eps[cs];
+                        const uint32_t zs = zeros ? zeros : 1u;
+                        const double den = __dsub_rn(g, __dmul_rn(g, eps));
+                        double est = __dmul_rn(-g, log(__ddiv_rn((double)zs, den)));
+                        if (est < 0.0) est = 0.0;
+                        // a cbaa_host record: {ip, z_union, est, flags}
+                        mybuf[nbuf] = make_uint4(unmangle(G, (lp[u] << G.r) | cs), zeros,
+                                                 __float_as_uint((float)est), zeros ? 0u : CBAA_FLAG_SATURATED);
+                    }
                 }
+                if (++nbuf == 32) flush();
             }
         }
     }
+    if (nbuf) flush();
 }
 
 // Host lists of up to kRankMax entries are sorted by rank: every thread owns
