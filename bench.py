@@ -276,14 +276,46 @@ def run_cbaa(args):
     out = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
     info = torch.zeros(8, dtype=torch.int32, device=dev)
     # update (direct: 1 kernel; binned: count, scan, scatter, apply) | detect: zero counts, eps/zmax,
-    # hot lists, |RA|-1 joins, sort
-    kernels_per_step = (4 if uws is not None else 1) + 3 + (geo["n_ra"] - 1) + 1
+    # hot lists, |RA|-1 joins, rank sort, sort/status
+    kernels_per_step = (4 if uws is not None else 1) + 3 + (geo["n_ra"] - 1) + 2
 
-    def do_update():
+    def do_update(c=None, src=None):
+        c = cube if c is None else c
+        src = pairs_dev if src is None else src
         if uws is not None:
-            cube.update_binned(pairs_dev, uws)
+            c.update_binned(src, uws)
         else:
-            cube.update(pairs_dev)
+            c.update(src)
+
+    # Double-buffered windows, as a deployed detector runs them: window k+1's
+    # reset and update (stream s_up, cube k+1 mod 2) overlap window k's detect
+    # (stream s_det, cube k mod 2); a cube is reset only after its previous
+    # detect finished.  Every window is fully updated and detected.
+    cubes2 = [cube, C.Cube(geo, device=dev)]
+    ws2 = [ws, C.Workspace(geo, max_candidates=1 << 18, device=dev)]
+    out2 = [out, torch.zeros(4 * cap, dtype=torch.int32, device=dev)]
+    info2 = [info, torch.zeros(8, dtype=torch.int32, device=dev)]
+    s_up, s_det = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    det_done = [None, None]
+
+    def piped_step(k):
+        b = k & 1
+        with torch.cuda.stream(s_up):
+            if det_done[b] is not None:
+                s_up.wait_event(det_done[b])
+            cubes2[b].reset()
+            do_update(cubes2[b])
+            up = torch.cuda.Event()
+            up.record(s_up)
+        with torch.cuda.stream(s_det):
+            s_det.wait_event(up)
+            cubes2[b].detect_async(theta, ws2[b], out2[b], info2[b])
+            det_done[b] = torch.cuda.Event()
+            det_done[b].record(s_det)
+
+    def join_streams():
+        stream.wait_stream(s_up)
+        stream.wait_stream(s_det)
 
     def step(ev=None):
         cube.reset()
@@ -330,44 +362,91 @@ def run_cbaa(args):
         if rep:
             direct_ms.append(e0.elapsed_time(e1))
 
-    # timed region
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    # serial steps, one window at a time: the update / detect split of a window
+    n_serial = max(3, min(args.steps, 50))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_serial)]
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for k in range(n_serial):
+        step(evs[k])
+    s1.record(stream)
+    torch.cuda.synchronize()
+    serial_ms = s0.elapsed_time(s1) / n_serial
+    upd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    det_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    hosts, inf = C.hosts_from_device(out, info)
+    assert inf["status"] == C.OK, inf
+
+    # timed region: double-buffered windows
+    for k in range(max(args.warmup, 0)):
+        piped_step(k)
+    join_streams()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         t_start.record(stream)
+        s_up.wait_stream(stream)
+        s_det.wait_stream(stream)
         for k in range(args.steps):
-            step(evs[k])
+            piped_step(k)
+        join_streams()
         t_end.record(stream)
         torch.cuda.synchronize()
     barrier(world)
     total_ms = t_start.elapsed_time(t_end)
     total_ms_max = reduce_over_ranks(total_ms, world, "max", dev)
-    upd_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    det_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    hosts, inf = C.hosts_from_device(out, info)
-    assert inf["status"] == C.OK, inf
+    for b in range(2):
+        h2, inf2 = C.hosts_from_device(out2[b], info2[b])
+        assert inf2["status"] == C.OK and inf2["n_hosts"] == inf["n_hosts"], (inf2, inf)
     packets_all = reduce_over_ranks(float(n), world, "sum", dev)
     value = packets_all * args.steps / (total_ms_max * 1e-3) / 1e9
 
-    # end to end through the public API with host buffers: H2D of the window's
-    # packets from pinned memory, update, synchronous detect with the host list
-    # copied back.
+    # end to end through the public API with host buffers, windows pipelined
+    # on three streams: H2D of window k+1's packets from pinned memory (s_copy)
+    # overlaps window k's update (s_up) and detect + D2H of its host list and
+    # info into pinned host memory (s_det).  Two device packet buffers.
     e2e_steps = max(3, min(args.steps, 10))
-    d2h = 0
+    bufs = [pairs_dev, torch.empty_like(pairs_dev)]
+    host_out = [torch.empty(4 * cap, dtype=torch.int32).pin_memory() for _ in range(2)]
+    host_info = [torch.empty(8, dtype=torch.int32).pin_memory() for _ in range(2)]
+    s_copy = torch.cuda.Stream(dev)
+    buf_free, det_done[0], det_done[1] = [None, None], None, None
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        pairs_dev.copy_(pairs_pin, non_blocking=True)
-        cube.reset()
-        do_update()
-        h = cube.detect(theta, ws=ws, cap=cap)
-        d2h += h.nbytes + C.INFO_BYTES
+    for k in range(e2e_steps):
+        b = k & 1
+        with torch.cuda.stream(s_copy):
+            if buf_free[b] is not None:
+                s_copy.wait_event(buf_free[b])
+            bufs[b].copy_(pairs_pin, non_blocking=True)
+            copied = torch.cuda.Event()
+            copied.record(s_copy)
+        with torch.cuda.stream(s_up):
+            s_up.wait_event(copied)
+            if det_done[b] is not None:
+                s_up.wait_event(det_done[b])
+            cubes2[b].reset()
+            do_update(cubes2[b], bufs[b])
+            up = torch.cuda.Event()
+            up.record(s_up)
+            buf_free[b] = up
+        with torch.cuda.stream(s_det):
+            s_det.wait_event(up)
+            cubes2[b].detect_async(theta, ws2[b], out2[b], info2[b])
+            host_out[b].copy_(out2[b], non_blocking=True)
+            host_info[b].copy_(info2[b], non_blocking=True)
+            det_done[b] = torch.cuda.Event()
+            det_done[b].record(s_det)
     torch.cuda.synchronize()
     e2e_s = reduce_over_ranks(time.perf_counter() - t0, world, "max", dev)
     e2e_value = packets_all * e2e_steps / e2e_s / 1e9
+    for b in range(2):
+        h2, inf2 = C.hosts_from_device(host_out[b], host_info[b])
+        assert inf2["status"] == C.OK and inf2["n_hosts"] == inf["n_hosts"], (inf2, inf)
+    d2h = host_out[0].numel() * 4 + host_info[0].numel() * 4
 
     hbm_peak, hbm_src = measured_peaks()
     upd_s = statistics.mean(upd_ms) * 1e-3
@@ -377,8 +456,12 @@ def run_cbaa(args):
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {**desc, "l2": "inputs larger than L2: each step streams a 512 MiB packet buffer; "
-                                 "the 64 MiB cube is L2-resident by design and re-zeroed every step",
+                                 "the 64 MiB cubes are L2-resident by design and re-zeroed every step",
+                   "pipelining": "double-buffered windows: a window's reset + update (stream 1, cube k mod 2) "
+                                 "overlaps the previous window's detect (stream 2)",
                    "parallelism": "one window per rank" if world > 1 else "single GPU"},
+        "serial": {"ms_per_window": serial_ms, "value": n / (serial_ms * 1e-3) / 1e9, "unit": "Gpps",
+                   "steps": n_serial, "note": "one window at a time on one stream (reset, update, detect)"},
         "update_ms": statistics.mean(upd_ms), "update_gpps": n / upd_s / 1e9,
         "detect_ms": statistics.mean(det_ms), "detect_ms_p50": statistics.median(det_ms),
         "hosts_detected": int(inf["n_hosts"]), "hot_columns": int(inf["n_hot"]),
@@ -403,8 +486,11 @@ def run_cbaa(args):
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_value, "unit": "Gpps", "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": int(d2h / e2e_steps), "steps": e2e_steps,
-                "path": "pinned host packets -> H2D -> cbaa_cube_update -> cbaa_detect (host list)"},
+                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+                "path": "pinned host packets -> H2D (stream 0) -> " +
+                        ("cbaa_cube_update_binned" if uws is not None else "cbaa_cube_update") +
+                        " (stream 1) -> cbaa_detect_async + D2H of the host list and info (stream 2), "
+                        "windows pipelined"},
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(geo, w.pairs, theta, min(n, args.reference_sample))
