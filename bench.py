@@ -591,13 +591,14 @@ def run_batched(args):
                        "router_loads": "lognormal(sigma=0.8) weights over a 5-tuple hash",
                        "geometry": "r=5, |RA|=3, |VA|=1, g=2^10, c=2^12 (64 MiB per cube)", "theta": theta,
                        "step": "one CUDA graph replay: per window reset router cubes, one partitioned update "
-                               "pass over all routers, OR-merge, detect",
+                               "pass over all routers, OR-merge into global cube w mod 2, detect on a side "
+                               "stream (overlapping the next window's router update)",
                        "l2": "inputs larger than L2 (2 GiB of packets per step)"},
             "window_ms": ms / steps / len(wins), "router_update_tiling": tiling,
             "plain_single_cube": {"value": plain_value, "unit": "Gpps", "window_ms": plain_ms / steps / len(wins),
                                   "path": "one cube, partitioned update of the whole window, detect, no graph"},
             "hosts_per_window": [int(i["n_hosts"]) for _, i in res],
-            "gpu_launches": steps * len(wins) * (4 + 1 + 3 + (geo["n_ra"] - 1) + 1),
+            "gpu_launches": steps * len(wins) * (4 + 1 + 3 + (geo["n_ra"] - 1) + 2),
             "clocks": clocks.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -7,8 +7,11 @@ Here the routers are local cubes on one GPU.  For each window the
 library's partitioned update feeds all router cubes in one pass (so uneven
 router loads share the whole GPU), the router cubes are OR-merged into the
 global cube, and the detect writes that window's host list to device
-memory.  A sequence of windows is recorded once into a CUDA graph and
-replayed with a single launch.
+memory.  The global cube is double-buffered: window w's detect runs on a
+side stream while window w+1's routers are reset and updated, as a global
+server detects one window while the routers scan the next.  A sequence of
+windows is recorded once into a CUDA graph (a fork/join over the two
+streams) and replayed with a single launch.
 
 Orchestration only: every step runs in libcbaa's kernels.
 """
@@ -25,26 +28,56 @@ class RouterWindows:
         torch = C._torch()
         self.geo, self.theta, self.cap = dict(geo), theta, cap
         self.routers = [C.Cube(geo, device=device) for _ in range(n_routers)]
-        self.glob = C.Cube(geo, device=device)
+        self.globs = [C.Cube(geo, device=device) for _ in range(2)]
         self.uws = C.UpdateWorkspace(geo, max_pairs, device=device, n_cubes=n_routers)
-        self.dws = C.Workspace(geo, max_candidates=max_candidates, device=device)
+        self.dws = [C.Workspace(geo, max_candidates=max_candidates, device=device) for _ in range(2)]
+        self.side = torch.cuda.Stream(device)
         self.out = torch.zeros((n_windows, 4 * cap), dtype=torch.int32, device=device)
         self.info = torch.zeros((n_windows, 8), dtype=torch.int32, device=device)
         self.graph = None
         self._keep = None
 
-    def enqueue_window(self, w: int, router_pairs, stream=None):
-        """One window: reset router cubes, one update pass over all of them, merge, detect."""
-        for c in self.routers:
-            c.reset(stream)
-        C.update_multi(self.routers, router_pairs, self.uws, stream=stream)
-        self.glob.reset(stream)
-        self.glob.merge(self.routers, stream)
-        self.glob.detect_async(self.theta, self.dws, self.out[w], self.info[w], stream)
+    @property
+    def glob(self):
+        """The global cube of the last enqueued window."""
+        return self.globs[(self._last_w if self._last_w is not None else 0) & 1]
 
-    def enqueue(self, windows, stream=None):
+    _last_w = None
+
+    def enqueue_window(self, w: int, router_pairs, done=None):
+        """One window on the current stream: reset router cubes, one update pass over all of them,
+        reset and merge into global cube w mod 2; its detect goes to the side stream.  `done[b]` is
+        the event after the last detect of global cube b (reset waits for it)."""
+        torch = C._torch()
+        main = torch.cuda.current_stream()
+        b = w & 1
+        for c in self.routers:
+            c.reset()
+        C.update_multi(self.routers, router_pairs, self.uws)
+        if done is not None and done[b] is not None:
+            main.wait_event(done[b])
+        self.globs[b].reset()
+        self.globs[b].merge(self.routers)
+        merged = torch.cuda.Event()
+        merged.record(main)
+        self.side.wait_event(merged)
+        with torch.cuda.stream(self.side):
+            self.globs[b].detect_async(self.theta, self.dws[b], self.out[w], self.info[w])
+            if done is not None:
+                done[b] = torch.cuda.Event()
+                done[b].record(self.side)
+        self._last_w = w
+
+    def enqueue(self, windows):
+        """All windows on the current stream; returns after the current stream has joined the side
+        stream, so everything enqueued is ordered before later work on the current stream."""
+        torch = C._torch()
+        main = torch.cuda.current_stream()
+        self.side.wait_stream(main)
+        done = [None, None]
         for w, rp in enumerate(windows):
-            self.enqueue_window(w, rp, stream)
+            self.enqueue_window(w, rp, done)
+        main.wait_stream(self.side)
 
     def tune(self, windows, reps: int = 3):
         """Pick the tiling of the partitioned update for these router cubes by timing the first window.
