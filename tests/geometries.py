@@ -44,7 +44,15 @@ TINY = _geo(6, 3, 1, 7, [10, 10, 10, 10], [0, 9, 18])
 # r=8, |RA|=3, |VA|=2, g=2^7, cbn=(9, 9, 10 | 7, 8).  L = 24: EP = (8, 8, 8), CP = (1, 1, 2).
 TINY2 = _geo(8, 3, 2, 7, [9, 9, 10, 7, 8], [0, 8, 16])
 
-ALL = dict(PAPER=PAPER, L2=L2, SERVE=SERVE, UNDERSIZED=UNDERSIZED, TINY=TINY, TINY2=TINY2)
+# Four restoring arrays (three join stages; the middle ones both extend and prune):
+# r=6, |RA|=4, |VA|=1, g=2^7, cbn=(10, 10, 10, 10 | 9).  L = 26: EP = (7, 7, 6, 6), CP = (3, 3, 4, 4).
+QUAD = _geo(6, 4, 1, 7, [10, 10, 10, 10, 9], [0, 7, 14, 20])
+
+# Two restoring arrays (one join stage that both opens and closes the ring) and two VAs:
+# r=6, |RA|=2, |VA|=2, g=2^7, cbn=(14, 14 | 10, 11).  L = 26: EP = (13, 13), CP = (1, 1).
+DUO = _geo(6, 2, 2, 7, [14, 14, 10, 11], [0, 13])
+
+ALL = dict(PAPER=PAPER, L2=L2, SERVE=SERVE, UNDERSIZED=UNDERSIZED, TINY=TINY, TINY2=TINY2, QUAD=QUAD, DUO=DUO)
 
 
 def with_form(d, form):

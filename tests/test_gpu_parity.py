@@ -63,7 +63,7 @@ def window(name):
 
 
 CUBE_CASES = [("TINY", "tiny"), ("TINY2", "tiny"), ("PAPER", "1m"), ("L2", "4m"), ("SERVE", "4m"),
-              ("UNDERSIZED", "4m")]
+              ("UNDERSIZED", "4m"), ("QUAD", "tiny"), ("DUO", "tiny")]
 
 
 @pytest.mark.parametrize("geo,win", CUBE_CASES)
@@ -226,7 +226,8 @@ def test_merge_geometry_mismatch(C):
 
 @pytest.mark.parametrize("geo,win,theta,form", [("TINY", "tiny", 128, 0), ("TINY2", "tiny", 128, 1),
                                                 ("PAPER", "1m", 1024, 0), ("L2", "4m", 1024, 0),
-                                                ("L2", "4m", 1024, 1), ("UNDERSIZED", "4m", 1024, 0)])
+                                                ("L2", "4m", 1024, 1), ("UNDERSIZED", "4m", 1024, 0),
+                                                ("QUAD", "tiny", 128, 0), ("DUO", "tiny", 128, 1)])
 def test_column_stats_bit_exact(C, oracle, geo, win, theta, form):
     d = GEO.with_form(GEO.ALL[geo], form)
     w = window(win)
@@ -250,7 +251,8 @@ def test_column_stats_bit_exact(C, oracle, geo, win, theta, form):
 DETECT_CASES = [("TINY", "tiny", 128, 0), ("TINY", "tiny", 96, 1), ("TINY", "tiny_sat", 128, 0),
                 ("TINY2", "tiny", 128, 0), ("PAPER", "1m", 1024, 0), ("PAPER", "1m", 1024, 1),
                 ("L2", "4m", 1024, 0), ("L2", "4m", 700, 1), ("UNDERSIZED", "4m", 1024, 0),
-                ("SERVE", "4m", 1024, 0)]
+                ("SERVE", "4m", 1024, 0), ("QUAD", "tiny", 128, 0),
+                ("DUO", "tiny", 128, 1)]
 
 
 @pytest.mark.parametrize("geo,win,theta,form", DETECT_CASES)

@@ -66,7 +66,7 @@ def test_mangle_roundtrip_and_ranges(oracle, name):
 
 # ------------------------------------------------------------------ column indices (Section III.B/C)
 
-@pytest.mark.parametrize("name", ["PAPER", "L2", "SERVE", "UNDERSIZED", "TINY", "TINY2"])
+@pytest.mark.parametrize("name", ["PAPER", "L2", "SERVE", "UNDERSIZED", "TINY", "TINY2", "QUAD", "DUO"])
 def test_ep_cp_structure(oracle, name):
     """EPs partition LP; CP(i) is the first |CP(i)| bits of the next column; LP is the EP concatenation."""
     d = GEO.ALL[name]
@@ -291,7 +291,8 @@ def test_linear_counting_expectation(oracle):
 
 # ------------------------------------------------------------------ Alg. 2 + Alg. 3 vs the plain definition
 
-CASES = [("TINY", 128, 0, 21), ("TINY", 96, 1, 22), ("TINY2", 128, 0, 23)]
+CASES = [("TINY", 128, 0, 21), ("TINY", 96, 1, 22), ("TINY2", 128, 0, 23), ("QUAD", 128, 0, 24),
+         ("DUO", 128, 1, 25)]
 
 
 @pytest.mark.parametrize("name,theta,form,seed", CASES)
