@@ -158,6 +158,27 @@ int cbaa_cube_params(const cbaa_cube *cube, cbaa_params *out);
 /* Zero every bit (async): the start of a new time window. */
 int cbaa_cube_reset(cbaa_cube *cube, void *stream);
 
+/* The monitored (inner) network NI of Section III as CIDR prefixes.  An
+ * edge router sees packets between NI and the outer network NO; the inner
+ * address of a packet may be its source or its destination, since a super
+ * host's peers are those it sends to or receives from (Def. 1). */
+#define CBAA_MAX_INNER 16
+typedef struct cbaa_inner_net {
+    uint32_t n;                        /* prefixes in use, 0..CBAA_MAX_INNER */
+    uint32_t addr[CBAA_MAX_INNER];     /* network address, host byte order */
+    uint32_t len[CBAA_MAX_INNER];      /* prefix length 0..32 (0 matches every address) */
+} cbaa_inner_net;
+
+/* Attach NI to a cube (host only; takes effect for updates enqueued after
+ * the call).  With n > 0 every update of this cube reads its pairs as raw
+ * {src, dst}: a pair with exactly one address in NI becomes {that address,
+ * the other} — its {iip, oip} — and a pair with both or neither address in
+ * NI (not traffic between NI and NO) is skipped.  net = NULL or n = 0
+ * restores the default, pairs given as {iip, oip}.  INVALID_ARG for n >
+ * CBAA_MAX_INNER or a length above 32; the cube's bits are untouched.  A
+ * multi-cube update requires the same NI on every cube. */
+int cbaa_cube_set_inner_net(cbaa_cube *cube, const cbaa_inner_net *net);
+
 /* Alg. 1 (Section III.B), async: for each of n pairs {iip, oip} at
  * dev_pairs (uint32[2n], 8-byte aligned; iip first) set bit H_bv(oip) in
  * the |RA|+|VA| columns that the mangled iip selects in its CS.  Bits are

@@ -225,6 +225,33 @@ def union_zeros(d, cube: np.ndarray, ip: int) -> int:
     return int(lib().oracle_union_zeros(_G(d), _p(cube, ctypes.c_uint32), ip))
 
 
+# --- the inner/outer model of Section III ----------------------------------------------------
+
+def in_prefixes(x: np.ndarray, prefixes) -> np.ndarray:
+    """True where address x lies in one of the CIDR prefixes [(address, length)] of NI."""
+    x = np.asarray(x, dtype=np.uint64)
+    hit = np.zeros(x.shape, dtype=bool)
+    for addr, length in prefixes:
+        mask = ((0xFFFFFFFF << (32 - length)) & 0xFFFFFFFF) if length else 0
+        hit |= (x & np.uint64(mask)) == np.uint64(int(addr) & mask)
+    return hit
+
+
+def orient(pairs: np.ndarray, prefixes) -> np.ndarray:
+    """Section III: an edge router relays packets between the inner network NI and the outer
+    network NO, and a host's peers are the outer addresses it sends to or receives from (Def. 1).
+    Each raw {src, dst} pair with exactly one address in NI becomes {inner, outer}; pairs with both
+    or neither address in NI are not traffic between NI and NO and are dropped.  Order is kept."""
+    pairs = np.asarray(pairs, dtype=np.uint32)
+    a_in = in_prefixes(pairs[:, 0], prefixes)
+    b_in = in_prefixes(pairs[:, 1], prefixes)
+    keep = a_in != b_in
+    out = pairs[keep].copy()
+    flip = b_in[keep]
+    out[flip] = out[flip][:, ::-1]
+    return out
+
+
 # --- exact baseline (Section V.A) and Eq. 2 / Eq. 3 -----------------------------------------
 
 def exact_counts(pairs: np.ndarray):

@@ -43,6 +43,13 @@ class DetectInfo(ctypes.Structure):
                 ("reserved", ctypes.c_uint32 * 3)]
 
 
+MAX_INNER = 16
+
+
+class InnerNet(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("addr", ctypes.c_uint32 * MAX_INNER), ("len", ctypes.c_uint32 * MAX_INNER)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("scatter_shape", ctypes.c_uint32), ("count_blocks_per_sm", ctypes.c_uint32),
                 ("apply_items_per_sm", ctypes.c_uint32), ("direct_blocks_per_sm", ctypes.c_uint32),
@@ -77,6 +84,7 @@ def _signatures():
         "cbaa_cube_data": (vp, [vp]),
         "cbaa_cube_params": (ctypes.c_int, [vp, P]),
         "cbaa_cube_reset": (ctypes.c_int, [vp, vp]),
+        "cbaa_cube_set_inner_net": (ctypes.c_int, [vp, ctypes.POINTER(InnerNet)]),
         "cbaa_cube_update": (ctypes.c_int, [vp, vp, sz, vp]),
         "cbaa_cube_merge": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.c_int, vp]),
         "cbaa_column_stats": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp, vp, vp, vp]),
@@ -279,6 +287,16 @@ class Cube:
 
     def reset(self, stream=None):
         _check(lib().cbaa_cube_reset(self.handle, _stream_ptr(stream)), "cube_reset")
+
+    def set_inner_net(self, prefixes=None):
+        """The monitored network NI as [(address, prefix length)] (addresses as ints, host order).
+        Afterwards updates read raw {src, dst} pairs and orient them; None or [] restores {iip, oip}."""
+        net = InnerNet()
+        prefixes = list(prefixes or [])
+        net.n = len(prefixes)
+        for k, (a, ln) in enumerate(prefixes[:MAX_INNER]):
+            net.addr[k], net.len[k] = int(a) & 0xFFFFFFFF, int(ln)
+        _check(lib().cbaa_cube_set_inner_net(self.handle, ctypes.byref(net)), "cube_set_inner_net")
 
     def update(self, pairs, n: int | None = None, stream=None):
         """pairs: device uint32/int32 tensor of shape [n, 2] (iip, oip), contiguous."""

@@ -180,6 +180,22 @@ int cbaa_cube_reset(cbaa_cube *cube, void *stream) {
     return cuda_status(cudaMemsetAsync(cube->data, 0, cube->bytes, as_stream(stream)));
 }
 
+int cbaa_cube_set_inner_net(cbaa_cube *cube, const cbaa_inner_net *net) {
+    if (!cube) return CBAA_ERR_INVALID_ARG;
+    const uint32_t k = net ? net->n : 0u;
+    if (k > CBAA_MAX_INNER) return CBAA_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < k; ++i)
+        if (net->len[i] > 32) return CBAA_ERR_INVALID_ARG;
+    cbaa::Geo &G = cube->G;
+    G.n_inner = k;
+    for (uint32_t i = 0; i < CBAA_MAX_INNER; ++i) {
+        const uint32_t mask = (i < k && net->len[i]) ? ~0u << (32 - net->len[i]) : 0u;
+        G.inner_mask[i] = mask;
+        G.inner_net[i] = i < k ? (net->addr[i] & mask) : 0u;
+    }
+    return CBAA_OK;
+}
+
 int cbaa_cube_update(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *stream) {
     if (!cube) return CBAA_ERR_INVALID_ARG;
     if (n == 0) return CBAA_OK;
@@ -218,6 +234,10 @@ int cbaa_cube_update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t 
         const cbaa_cube *c = cubes[j];
         if (!c) return CBAA_ERR_INVALID_ARG;
         if (std::memcmp(&c->p, &c0->p, sizeof(cbaa_params)) != 0) return CBAA_ERR_GEOMETRY;
+        if (c->G.n_inner != G.n_inner ||
+            std::memcmp(c->G.inner_net, G.inner_net, sizeof G.inner_net) != 0 ||
+            std::memcmp(c->G.inner_mask, G.inner_mask, sizeof G.inner_mask) != 0)
+            return CBAA_ERR_INVALID_ARG;                 // one NI for all cubes of a pass
         for (int i = 0; i < j; ++i)
             if (cubes[i] == c) return CBAA_ERR_INVALID_ARG;
         S.cube[j] = c->data;

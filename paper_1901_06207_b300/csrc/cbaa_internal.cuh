@@ -28,6 +28,9 @@ struct Geo {
     uint32_t col_base[CBAA_MAX_ARRAYS + 1];  // arr_base / W: first column of array a among a CS's columns
     uint32_t cs_words;                       // words of one CS
     uint64_t cube_words;
+    uint32_t n_inner;                        // NI prefixes (0: pairs arrive as {iip, oip})
+    uint32_t inner_net[CBAA_MAX_INNER];      // prefix addresses, masked
+    uint32_t inner_mask[CBAA_MAX_INNER];     // prefix masks
 };
 
 // Builds Geo from validated params (host).
@@ -87,6 +90,24 @@ __host__ __device__ __forceinline__ uint32_t ra_col(const Geo &G, uint32_t i, ui
     const uint32_t off = G.ring_off[i];
     uint32_t v = (lp >> off) | (lp << (G.L - off));   // L - off in [1, 31] since r >= 1
     return v & ((1u << G.cbn[i]) - 1u);
+}
+
+// Section III: a packet between NI and NO carries exactly one inner address.
+// Puts it first ({iip, oip}) and returns true; returns false for a packet
+// with both or neither address in NI.  Only called when G.n_inner > 0.
+__host__ __device__ __forceinline__ bool orient(const Geo &G, uint32_t &a, uint32_t &b) {
+    bool ia = false, ib = false;
+    for (uint32_t k = 0; k < G.n_inner; ++k) {
+        ia |= ((a & G.inner_mask[k]) == G.inner_net[k]);
+        ib |= ((b & G.inner_mask[k]) == G.inner_net[k]);
+    }
+    if (ia == ib) return false;
+    if (ib) {
+        const uint32_t t = a;
+        a = b;
+        b = t;
+    }
+    return true;
 }
 
 #ifdef __CUDACC__

@@ -29,6 +29,7 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
 // time (the common 3+1 layout); 0 reads them from G.
 template <int NRA, int NVA>
 __device__ __forceinline__ void apply_pair(const Geo &G, uint32_t *__restrict__ cube, uint32_t iip, uint32_t oip) {
+    if (G.n_inner && !orient(G, iip, oip)) return;      // raw {src, dst} against NI (Section III)
     const uint32_t nra = NRA ? NRA : G.n_ra;
     const uint32_t nva = NRA ? NVA : G.n_va;
     const uint32_t row = row_of(G, oip);

@@ -178,7 +178,14 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(const Geo G, const 
             seg[u] = 0xFFFFFFFFu;
             if (p < n) {
                 seg[u] = seg_of(S, p);
-                iip[u] = ld_stream_u32(S.pairs[seg[u]] + 2 * (p - S.start[seg[u]]));
+                const uint32_t *pp = S.pairs[seg[u]] + 2 * (p - S.start[seg[u]]);
+                if (G.n_inner) {                          // raw {src, dst} against NI (Section III)
+                    uint2 v = ld_pair(pp);
+                    if (orient(G, v.x, v.y)) iip[u] = v.x;
+                    else seg[u] = 0xFFFFFFFFu;
+                } else {
+                    iip[u] = ld_stream_u32(pp);
+                }
             }
         }
 #pragma unroll
@@ -238,14 +245,18 @@ __global__ void __launch_bounds__(THREADS) k_bin_scatter(const Geo G, const BinS
     __syncthreads();
     // codes packed as tile << (kTileBits + 5) | word-in-tile << 5 | bit, kept in registers
     uint32_t code[PPT][AM];
+    bool ok[PPT];
     uint32_t A = G.A;
 #pragma unroll
     for (uint32_t k = 0; k < PPT; ++k) {
         const uint32_t p = threadIdx.x + k * THREADS;
+        ok[k] = false;
         if (p < np) {
             const uint64_t gp = p0 + p;
             const uint32_t s = seg_of(S, gp);
-            const uint2 v = ld_pair(S.pairs[s] + 2 * (gp - S.start[s]));
+            uint2 v = ld_pair(S.pairs[s] + 2 * (gp - S.start[s]));
+            if (G.n_inner && !orient(G, v.x, v.y)) continue;   // raw {src, dst} against NI (Section III)
+            ok[k] = true;
             uint32_t w[AM], bit;
             A = pair_targets<NRA, NVA>(G, S.router[s] * S.seg_words, v.x, v.y, w, bit);
 #pragma unroll
@@ -266,8 +277,7 @@ __global__ void __launch_bounds__(THREADS) k_bin_scatter(const Geo G, const BinS
     __syncthreads();
 #pragma unroll
     for (uint32_t k = 0; k < PPT; ++k) {
-        const uint32_t p = threadIdx.x + k * THREADS;
-        if (p < np) {
+        if (ok[k]) {
 #pragma unroll
             for (uint32_t a = 0; a < AM; ++a) {
                 if (NRA == 0 && a >= A) break;

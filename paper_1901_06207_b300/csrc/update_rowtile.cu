@@ -134,7 +134,8 @@ __device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
 // once; any other tile packet by packet.
 constexpr uint32_t kCountTile = 4 * kCountThreads;
 
-template <bool MULTI>
+// ORIENT (the cube has an inner network): packets are raw {src, dst} (orient()).
+template <bool MULTI, bool ORIENT>
 __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                             uint32_t *__restrict__ counts) {
     extern __shared__ uint32_t hist[];
@@ -168,15 +169,18 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
             const uint4 q0 = ld_quad(ptr + 4 * threadIdx.x);
             const uint4 q1 = ld_quad(ptr + 4 * (threadIdx.x + kCountThreads));
             const uint32_t rb = B.unit(S, s) * B.tpr;
-            const uint32_t ip[4] = {q0.x, q0.z, q1.x, q1.z}, oip[4] = {q0.y, q0.w, q1.y, q1.w};
+            uint32_t ip[4] = {q0.x, q0.z, q1.x, q1.z}, oip[4] = {q0.y, q0.w, q1.y, q1.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                if (ORIENT && !orient(G, ip[u], oip[u])) continue;      // raw {src, dst} against NI
                 atomicAdd(&hist[rb + row_tile(G, 0, mangle(G, ip[u]), row_of(G, oip[u]))], 1u);
+            }
         } else {
             const uint64_t end = base + kCountTile < hi ? base + kCountTile : hi;
             for (uint64_t p = base + threadIdx.x; p < end; p += kCountThreads) {
                 const uint32_t sp = seg_of(S, p);
-                const uint2 v = ld_pair(S.pairs[sp] + 2 * (p - S.start[sp]));
+                uint2 v = ld_pair(S.pairs[sp] + 2 * (p - S.start[sp]));
+                if (ORIENT && !orient(G, v.x, v.y)) continue;
                 atomicAdd(&hist[row_tile(G, B.unit(S, sp), mangle(G, v.x), row_of(G, v.y))], 1u);
             }
         }
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
 // SHORT records (r >= 5): lp << 5 | bit in 4 bytes; else {mangled ip, row}.
 // Shapes of up to 8 packets per thread are held to 32 registers (4-byte
 // records: 2048 threads per SM, measured ~8 % faster) or 42 (8-byte records).
-template <int THREADS, int PPT, bool SHORT, bool MULTI>
+template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT>
 __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) / THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                         uint32_t *__restrict__ cursors, void *__restrict__ recs_out) {
     extern __shared__ uint32_t sm[];
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     for (uint32_t k = 0; k < PPT; ++k) {
         slot[k] = 0xFFFFFFFFu;
         if (rt[k] != 0xFFFFFFFFu) {
+            if (ORIENT && !orient(G, rec[k].x, rec[k].y)) continue;      // raw {src, dst} against NI
             const uint32_t m = mangle(G, rec[k].x), row = row_of(G, rec[k].y);
             const uint32_t b = row_tile(G, rt[k], m, row);
             if (SHORT) rec[k].x = ((m >> G.r) << 5) | (row & 31u);
@@ -388,30 +393,37 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaSuccess;
 }
 
-template <int THREADS, int PPT, bool SHORT, bool MULTI>
+template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT>
 cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                               cudaStream_t s) {
     const size_t per = SHORT ? 2 : 3;                 // staged record words + bin word per packet
     const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nb + 1) & ~(size_t)1) + per * THREADS * PPT);
-    cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT, SHORT, MULTI>, smem);
+    cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT>, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
-    k_rt_scatter<THREADS, PPT, SHORT, MULTI><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes);
+    k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes);
     return cudaGetLastError();
 }
 
-template <bool SHORT, bool MULTI>
+template <bool SHORT, bool MULTI, bool ORIENT>
 cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                                     uint32_t shape, cudaStream_t s) {
     switch (shape) {
-        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI>(G, S, m, nb, W, s);
-        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI>(G, S, m, nb, W, s);
-        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI>(G, S, m, nb, W, s);
-        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI>(G, S, m, nb, W, s);
-        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI>(G, S, m, nb, W, s);
-        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI>(G, S, m, nb, W, s);
-        default: return launch_rt_scatter<512, 8, SHORT, MULTI>(G, S, m, nb, W, s);
+        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        default: return launch_rt_scatter<512, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
     }
+}
+
+template <bool MULTI, bool ORIENT>
+cudaError_t launch_rt_scatter_kind(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
+                                   uint32_t shape, cudaStream_t s) {
+    return G.r >= 5 ? launch_rt_scatter_shape<true, MULTI, ORIENT>(G, S, m, nb, W, shape, s)
+                    : launch_rt_scatter_shape<false, MULTI, ORIENT>(G, S, m, nb, W, shape, s);
 }
 
 template <typename Rec>
@@ -443,9 +455,10 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
     const int sms = num_sms();
     const size_t apply_smem = sizeof(uint32_t) * tw;
     cudaError_t e;
-    const bool multi = S0.n_routers > 1;
-    if ((e = allow_smem(multi ? k_rt_count<true> : k_rt_count<false>, sizeof(uint32_t) * nb)) != cudaSuccess)
-        return e;
+    const bool multi = S0.n_routers > 1, ori = G.n_inner > 0;
+    auto kcount = multi ? (ori ? k_rt_count<true, true> : k_rt_count<true, false>)
+                        : (ori ? k_rt_count<false, true> : k_rt_count<false, false>);
+    if ((e = allow_smem(kcount, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
     const bool short_rec = G.r >= 5;                  // lp (32 - r bits) and the bit fit one word
     const uint64_t rec_words = short_rec ? 1 : 2;
     const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
@@ -469,19 +482,18 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
         const uint64_t want = (m + kCountTile - 1) / kCountTile;
         const uint64_t cap = (uint64_t)sms * count_bps;
         const unsigned cgrid = (unsigned)(want < cap ? want : cap);
-        if (multi) k_rt_count<true><<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts);
-        else k_rt_count<false><<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts);
+        kcount<<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // split a row tile only when it holds more than apply_ips/2 times the average tile
         uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
         if (ch < (1u << 12)) ch = 1u << 12;
         if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s)) != cudaSuccess) return e;
         if (multi)
-            e = short_rec ? launch_rt_scatter_shape<true, true>(G, S, m, nb, W, T.scatter_shape, s)
-                          : launch_rt_scatter_shape<false, true>(G, S, m, nb, W, T.scatter_shape, s);
+            e = ori ? launch_rt_scatter_kind<true, true>(G, S, m, nb, W, T.scatter_shape, s)
+                    : launch_rt_scatter_kind<true, false>(G, S, m, nb, W, T.scatter_shape, s);
         else
-            e = short_rec ? launch_rt_scatter_shape<true, false>(G, S, m, nb, W, T.scatter_shape, s)
-                          : launch_rt_scatter_shape<false, false>(G, S, m, nb, W, T.scatter_shape, s);
+            e = ori ? launch_rt_scatter_kind<false, true>(G, S, m, nb, W, T.scatter_shape, s)
+                    : launch_rt_scatter_kind<false, false>(G, S, m, nb, W, T.scatter_shape, s);
         if (e != cudaSuccess) return e;
         e = short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s)
                       : launch_rt_apply<uint2>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s);

@@ -39,6 +39,7 @@ _MASK32 = np.uint64(0xFFFFFFFF)
 
 # stream tags (any distinct constants)
 S_HOSTS, S_PLANT_N, S_BG_N, S_PEERS, S_BG_SRC, S_DUP, S_SHUF, S_PORTS, S_ROUTER_W = range(1, 10)
+S_DIR, S_NOISE = 10, 11
 
 
 def splitmix64(x: np.ndarray) -> np.ndarray:
@@ -241,3 +242,31 @@ def router_window(spec: TrafficSpec, n_routers: int, sigma: float = 0.8):
     order = np.argsort(rid, kind="stable")
     counts = np.bincount(rid, minlength=n_routers).astype(np.int64)
     return np.ascontiguousarray(w.pairs[order]), counts, weights
+
+
+def bidirectional_pairs(pairs: np.ndarray, seed: int, prefix: int, length: int, flip: float = 0.5,
+                        internal: float = 0.02, transit: float = 0.02) -> np.ndarray:
+    """Raw {src, dst} packets of an edge router between an inner network NI = prefix/length and
+    the outer network (Section III), made from a window of <inner, outer> pairs: the inner
+    address is moved into NI (its low 32 - length bits kept), an outer address that falls in NI
+    is moved out of it, a fraction ``flip`` of the packets travel inward (the pair reversed), and
+    fractions ``internal`` / ``transit`` of the packets are replaced by NI-to-NI and
+    outside-to-outside packets, which are not traffic between NI and NO."""
+    pairs = np.asarray(pairs, dtype=np.uint32)
+    n = pairs.shape[0]
+    mask = ((0xFFFFFFFF << (32 - length)) & 0xFFFFFFFF) if length else 0
+    net = np.uint32(prefix & mask)
+    inner = (pairs[:, 0] & np.uint32(~mask & 0xFFFFFFFF)) | net
+    outer = pairs[:, 1].copy()
+    hit = (outer & np.uint32(mask)) == net
+    outer[hit] ^= np.uint32(0x80000000 if length else 0)       # out of NI (length >= 1)
+    out = np.stack([inner, outer], axis=1)
+    v = rand_unit(seed, S_NOISE, n)
+    k_int = v < internal
+    k_tr = (v >= internal) & (v < internal + transit)
+    out[k_int, 1] = out[k_int, 0] ^ np.uint32(1)               # the inner neighbour (length <= 31)
+    out[k_tr, 0] = out[k_tr, 1] ^ np.uint32(1)                 # the outer neighbour of the peer
+    u = rand_unit(seed, S_DIR, n)
+    out[u < flip] = out[u < flip][:, ::-1]
+    return out
+

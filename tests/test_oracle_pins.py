@@ -350,3 +350,68 @@ def test_fnr_fpr_definitions(oracle):
     # H = {1, 2, 5}; detected {1, 3, 9}: FN = {2, 5}, FP = {3, 9 (never seen)}
     fnr, fpr, nH = oracle.fnr_fpr(np.array([1, 3, 9]), ips, cnt, 1024)
     assert nH == 3 and fnr == pytest.approx(2 / 3) and fpr == pytest.approx(2 / 3)
+
+
+# ------------------------------------------------------------------ the inner/outer model (Section III)
+
+def _ip(s: str) -> int:
+    return int.from_bytes(bytes(int(x) for x in s.split(".")), "big")
+
+
+def test_orient_cases_from_section_iii(oracle):
+    """Hand-derived from Section III: a packet between NI and NO keeps its inner address first,
+    whichever direction it travels; internal (both in NI) and transit (neither) packets are not
+    between NI and NO.  Prefix edges: 172.16.0.0/12 spans 172.16.0.0 .. 172.31.255.255."""
+    ni = [(_ip("10.0.0.0"), 8), (_ip("172.16.0.0"), 12), (_ip("192.0.2.7"), 32)]
+    cases = [(("10.1.2.3", "8.8.8.8"), ("10.1.2.3", "8.8.8.8")),
+             (("8.8.8.8", "10.1.2.3"), ("10.1.2.3", "8.8.8.8")),
+             (("10.0.0.1", "10.200.0.2"), None),
+             (("1.1.1.1", "2.2.2.2"), None),
+             (("172.31.255.255", "172.32.0.0"), ("172.31.255.255", "172.32.0.0")),
+             (("172.32.0.0", "172.16.0.0"), ("172.16.0.0", "172.32.0.0")),
+             (("172.15.255.255", "172.32.0.0"), None),
+             (("192.0.2.8", "192.0.2.7"), ("192.0.2.7", "192.0.2.8")),
+             (("11.0.0.0", "9.255.255.255"), None)]
+    raw = np.array([[_ip(a), _ip(b)] for (a, b), _ in cases], dtype=np.uint32)
+    want = np.array([[_ip(a), _ip(b)] for _, w in cases if w for a, b in [w]], dtype=np.uint32)
+    assert np.array_equal(oracle.orient(raw, ni), want)
+
+
+def test_orient_edge_prefixes_and_direction_blindness(oracle):
+    rng = np.random.default_rng(12)
+    pairs = rng.integers(0, 1 << 32, size=(5000, 2), dtype=np.uint64).astype(np.uint32)
+    assert oracle.orient(pairs, [(0, 0)]).shape == (0, 2)          # /0: every address inner
+    assert oracle.orient(pairs, []).shape == (0, 2)                # empty NI: every address outer
+    ni = [(_ip("10.0.0.0"), 8)]
+    inner = (_ip("10.0.0.0") | (rng.integers(0, 1 << 24, 5000))).astype(np.uint32)
+    outer = rng.integers(0, 1 << 32, 5000, dtype=np.uint64).astype(np.uint32)
+    outer = outer[(outer >> 24) != 10]
+    inner = inner[: outer.size]
+    fwd = np.stack([inner, outer], axis=1)
+    flip = rng.random(inner.size) < 0.5
+    raw = fwd.copy()
+    raw[flip] = raw[flip][:, ::-1]
+    assert np.array_equal(oracle.orient(raw, ni), fwd)
+    assert np.array_equal(oracle.orient(fwd, ni), fwd)
+
+
+def test_host_with_peers_in_both_directions(oracle):
+    """Def. 1 counts peers a host sends to or receives from: one host in an empty cube whose
+    peers arrive half as destinations, half as sources, plus internal and transit noise,
+    has Z_U = g - |distinct rows of its peers|."""
+    d = GEO.L2
+    g = 1 << d["log2_g"]
+    ni = [(_ip("10.20.0.0"), 16)]
+    rng = np.random.default_rng(13)
+    host = _ip("10.20.3.4")
+    peers = rng.choice(np.arange(1 << 31, 1 << 32, dtype=np.uint64), size=700, replace=False).astype(np.uint32)
+    out_dir = np.stack([np.full(350, host, np.uint32), peers[:350]], axis=1)
+    in_dir = np.stack([peers[350:], np.full(350, host, np.uint32)], axis=1)
+    internal = np.array([[host, _ip("10.20.9.9")]] * 40, dtype=np.uint32)
+    transit = np.stack([peers[:40], peers[40:80]], axis=1)
+    raw = np.concatenate([out_dir, in_dir, internal, transit])
+    raw = raw[rng.permutation(raw.shape[0])]
+    cube = oracle.build_cube(d, oracle.orient(raw, ni))
+    rows = {oracle.row(d, int(p)) for p in peers}
+    assert oracle.union_zeros(d, cube, host) == g - len(rows)
+    assert int(np.count_nonzero(cube)) <= 4 * (g // 32)          # only the host's A columns are touched
