@@ -447,6 +447,17 @@ def run_cbaa(args):
         h2, inf2 = C.hosts_from_device(host_out[b], host_info[b])
         assert inf2["status"] == C.OK and inf2["n_hosts"] == inf["n_hosts"], (inf2, inf)
     d2h = host_out[0].numel() * 4 + host_info[0].numel() * 4
+    # the e2e bound: a plain pinned host-to-device copy of one window's packets, alone
+    h2d_rates = []
+    for rep in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bufs[1].copy_(pairs_pin, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            h2d_rates.append(8 * n / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    h2d_peak = max(h2d_rates)
 
     hbm_peak, hbm_src = measured_peaks()
     upd_s = statistics.mean(upd_ms) * 1e-3
@@ -490,7 +501,11 @@ def run_cbaa(args):
                 "path": "pinned host packets -> H2D (stream 0) -> " +
                         ("cbaa_cube_update_binned" if uws is not None else "cbaa_cube_update") +
                         " (stream 1) -> cbaa_detect_async + D2H of the host list and info (stream 2), "
-                        "windows pipelined"},
+                        "windows pipelined",
+                "roofline": {"bound": "h2d", "achieved": e2e_value * 8, "peak": h2d_peak, "unit": "GB/s",
+                             "frac": e2e_value * 8 / h2d_peak,
+                             "peak_source": "pinned host-to-device copy of one window's packets alone, "
+                                            "measured in this run"}},
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(geo, w.pairs, theta, min(n, args.reference_sample))

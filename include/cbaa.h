@@ -247,6 +247,23 @@ int cbaa_column_stats(const cbaa_cube *cube, uint32_t theta, uint16_t *dev_zc, u
 int cbaa_detect_async(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_bytes,
                       cbaa_host *dev_out, size_t cap, cbaa_detect_info *dev_info, void *stream);
 
+/* Sharded restoration (Section III.C with the global server's work split
+ * by sketch): cbaa_detect_async restricted to the sketches cs_lo <= cs <
+ * cs_hi (cs = the right r bits of the mangled address).  Detection is
+ * independent per sketch (each has its own eps and Zmax), so the host lists
+ * of disjoint ranges covering [0, 2^r) together are exactly the full host
+ * list.  INVALID_ARG unless cs_lo < cs_hi <= 2^r. */
+int cbaa_detect_range_async(const cbaa_cube *cube, uint32_t cs_lo, uint32_t cs_hi, uint32_t theta, void *dev_ws,
+                            size_t ws_bytes, cbaa_host *dev_out, size_t cap, cbaa_detect_info *dev_info,
+                            void *stream);
+
+/* The OR of Section III.C on raw words, async: dst[i] |= src_0[i] | ... |
+ * src_{k-1}[i] for i < words.  For sharded merges, where each owner ORs
+ * the slices of its sketches received from the other routers.  dst and
+ * every src 16-byte aligned device pointers, words a multiple of 4, dst
+ * not among srcs; k = 0 or words = 0 is a no-op. */
+int cbaa_or_words(uint32_t *dst, const uint32_t *const *srcs, int k, size_t words, void *stream);
+
 /* Same as cbaa_detect_async followed by the copy of the records to host_out
  * (room for cap) and *n_out = number of hosts found; sync.  Returns
  * CBAA_ERR_CAPACITY when n_hosts > cap (the first cap records are valid) and

@@ -89,6 +89,9 @@ def _signatures():
         "cbaa_cube_merge": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.c_int, vp]),
         "cbaa_column_stats": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp, vp, vp, vp]),
         "cbaa_detect_async": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, sz, vp, vp]),
+        "cbaa_detect_range_async": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp, sz,
+                                                   vp, sz, vp, vp]),
+        "cbaa_or_words": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.c_int, sz, vp]),
         "cbaa_detect": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, sz, ctypes.POINTER(sz), vp]),
         "cbaa_bench_red_or": (ctypes.c_int, [vp, sz, sz, ctypes.c_uint32, vp]),
         "cbaa_detect_static": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, vp]),
@@ -365,6 +368,23 @@ class Cube:
         cap = out.numel() * out.element_size() // 16
         _check(lib().cbaa_detect_async(self.handle, theta, ws.ptr, ws.nbytes, out.data_ptr(), cap,
                                        info.data_ptr(), _stream_ptr(stream)), "detect_async")
+
+
+    def detect_range_async(self, cs_lo: int, cs_hi: int, theta: int, ws: Workspace, out, info, stream=None):
+        """detect_async restricted to the sketches cs_lo <= cs < cs_hi."""
+        cap = out.numel() * out.element_size() // 16
+        _check(lib().cbaa_detect_range_async(self.handle, cs_lo, cs_hi, theta, ws.ptr, ws.nbytes, out.data_ptr(), cap,
+                                             info.data_ptr(), _stream_ptr(stream)), "detect_range_async")
+
+
+def or_words(dst, srcs, stream=None):
+    """dst |= OR of srcs, word by word (device int32/uint32 tensors of equal length, 16-byte aligned)."""
+    words = dst.numel() * dst.element_size() // 4
+    for t in srcs:
+        if t.numel() * t.element_size() // 4 != words:
+            raise ValueError("or_words: every source must have dst's length")
+    arr = (ctypes.c_void_p * max(1, len(srcs)))(*[t.data_ptr() for t in srcs])
+    _check(lib().cbaa_or_words(dst.data_ptr(), arr, len(srcs), words, _stream_ptr(stream)), "or_words")
 
 
 def hosts_from_device(out, info) -> tuple[np.ndarray, dict]:

@@ -314,6 +314,25 @@ int cbaa_detect_async(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_
                                 cbaa::num_sms(), as_stream(stream));
 }
 
+int cbaa_detect_range_async(const cbaa_cube *cube, uint32_t cs_lo, uint32_t cs_hi, uint32_t theta, void *dev_ws,
+                            size_t ws_bytes, cbaa_host *dev_out, size_t cap, cbaa_detect_info *dev_info,
+                            void *stream) {
+    if (!cube || !dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u) || !dev_info || (cap > 0 && !dev_out))
+        return CBAA_ERR_INVALID_ARG;
+    if (cs_lo >= cs_hi || cs_hi > cube->G.smask + 1) return CBAA_ERR_INVALID_ARG;
+    return cbaa::detect_enqueue(cube->G, cube->data, theta, dev_ws, ws_bytes, dev_out, cap, dev_info,
+                                cbaa::num_sms(), as_stream(stream), cs_lo, cs_hi);
+}
+
+int cbaa_or_words(uint32_t *dst, const uint32_t *const *srcs, int k, size_t words, void *stream) {
+    if (k < 0 || (k > 0 && words > 0 && (!dst || !srcs))) return CBAA_ERR_INVALID_ARG;
+    if (k == 0 || words == 0) return CBAA_OK;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15u) || (words & 3u)) return CBAA_ERR_INVALID_ARG;
+    for (int j = 0; j < k; ++j)
+        if (!srcs[j] || srcs[j] == dst || (reinterpret_cast<uintptr_t>(srcs[j]) & 15u)) return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_merge(dst, srcs, k, words, as_stream(stream)));
+}
+
 int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_bytes, cbaa_host *host_out, size_t cap,
                 size_t *n_out, void *stream) {
     if (!cube || !dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u) || !n_out || (cap > 0 && !host_out))

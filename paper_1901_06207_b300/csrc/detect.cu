@@ -37,8 +37,8 @@ static_assert(sizeof(cbaa_host) == 16 && offsetof(cbaa_host, z_union) == 4 && of
 // than Zmax zero bits.  For i = 0 the hot columns become the seed tuples
 // (cs, hc_0) of the join; for i >= 1 they are stored key-major (key = low
 // |CP(i-1)| bits) with bucket offsets.
-__global__ void __launch_bounds__(1024) k_hot_lists(const Geo G, WsPtrs P) {
-    const uint32_t cs = blockIdx.x, i = blockIdx.y;
+__global__ void __launch_bounds__(1024) k_hot_lists(const Geo G, WsPtrs P, uint32_t cs_lo) {
+    const uint32_t cs = cs_lo + blockIdx.x, i = blockIdx.y;
     const uint32_t ncol = 1u << G.cbn[i];
     const int64_t zm = P.zmax[cs];
     const uint32_t kb = (i == 0) ? 0u : G.cp[i - 1];
@@ -359,7 +359,10 @@ cudaError_t launch_join(const Geo &G, const uint32_t *cube, const WsPtrs &P, uin
 }  // namespace
 
 int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws, size_t ws_bytes,
-                   cbaa_host *out, uint64_t cap, cbaa_detect_info *info_copy, int num_sms, cudaStream_t s) {
+                   cbaa_host *out, uint64_t cap, cbaa_detect_info *info_copy, int num_sms, cudaStream_t s,
+                   uint32_t cs_lo, uint32_t cs_hi) {
+    if (cs_hi == 0) cs_hi = G.smask + 1;
+    if (cs_lo >= cs_hi || cs_hi > G.smask + 1) return CBAA_ERR_INVALID_ARG;
     WsLayout Ly;
     if (!ws_layout_fit(G, ws_bytes, &Ly)) return CBAA_ERR_WORKSPACE;
     WsPtrs P = ws_pointers(G, Ly, ws);
@@ -367,9 +370,9 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
 
     cudaError_t e = cudaMemsetAsync(P.state, 0, sizeof(DevState), s);
     if (e != cudaSuccess) return CBAA_ERR_CUDA;
-    e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s);
+    e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s, cs_lo, cs_hi);
     if (e != cudaSuccess) return CBAA_ERR_CUDA;
-    k_hot_lists<<<dim3(G.smask + 1, G.n_ra), 1024, 0, s>>>(G, P);
+    k_hot_lists<<<dim3(cs_hi - cs_lo, G.n_ra), 1024, 0, s>>>(G, P, cs_lo);
     if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
     const unsigned blocks = (unsigned)num_sms * 4;
     const uint32_t wpl = G.W >= 32 ? G.W / 32 : 1;

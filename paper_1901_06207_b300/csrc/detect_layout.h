@@ -116,7 +116,9 @@ inline WsPtrs ws_pointers(const Geo &G, const WsLayout &L, void *base) {
     return P;
 }
 
+// Restoration of the sketches [cs_lo, cs_hi) (cs_hi = 0: all of them).
 int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws, size_t ws_bytes,
-                   cbaa_host *out, uint64_t cap, cbaa_detect_info *info_copy, int num_sms, cudaStream_t s);
+                   cbaa_host *out, uint64_t cap, cbaa_detect_info *info_copy, int num_sms, cudaStream_t s,
+                   uint32_t cs_lo = 0, uint32_t cs_hi = 0);
 
 }  // namespace cbaa

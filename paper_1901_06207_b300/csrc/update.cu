@@ -116,8 +116,9 @@ __global__ void __launch_bounds__(256) k_merge(uint4 *__restrict__ dst, const Sr
 
 __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t *__restrict__ cube,
                                                      uint16_t *__restrict__ zc,
-                                                     unsigned long long *__restrict__ za, uint32_t splits) {
-    const uint32_t arr = blockIdx.x;                 // cs*A + a
+                                                     unsigned long long *__restrict__ za, uint32_t splits,
+                                                     uint32_t arr0) {
+    const uint32_t arr = arr0 + blockIdx.x;          // cs*A + a
     const uint32_t cs = arr / G.A, a = arr % G.A;
     const uint32_t ncol = 1u << G.cbn[a];
     const uint32_t c0 = (uint32_t)(((uint64_t)ncol * blockIdx.y) / splits);
@@ -172,9 +173,10 @@ __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t
 // operation is a correctly rounded IEEE double operation in a fixed order
 // (explicit _rn intrinsics, so nothing is contracted into an FMA).
 __global__ void k_eps_zmax(const Geo G, const unsigned long long *__restrict__ za, double E,
-                           double *__restrict__ eps_out, int64_t *__restrict__ zmax_out) {
-    const uint32_t cs = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cs > G.smask) return;
+                           double *__restrict__ eps_out, int64_t *__restrict__ zmax_out, uint32_t cs_lo,
+                           uint32_t cs_hi) {
+    const uint32_t cs = cs_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (cs >= cs_hi) return;
     double eps = 1.0;
     for (uint32_t a = 0; a < G.A; ++a) {
         const unsigned long long bits = (unsigned long long)(1u << G.cbn[a]) << G.log2_g;
@@ -242,21 +244,26 @@ cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint
 }
 
 cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc, uint64_t *za,
-                                double *eps, int64_t *zmax, double E, cudaStream_t s) {
+                                double *eps, int64_t *zmax, double E, cudaStream_t s, uint32_t cs_lo,
+                                uint32_t cs_hi) {
+    if (cs_hi == 0) cs_hi = G.smask + 1;
     cudaError_t e = cudaMemsetAsync(za, 0, sizeof(uint64_t) * (size_t)(G.smask + 1) * G.A, s);
     if (e != cudaSuccess) return e;
-    const uint32_t arrays = (G.smask + 1) * G.A;
+    if (cs_lo >= cs_hi) return cudaSuccess;
+    const uint32_t arrays = (cs_hi - cs_lo) * G.A;
     // Enough blocks to cover every SM several times; each slice is whole columns.
     uint32_t splits = 1;
     while ((uint64_t)arrays * splits < (uint64_t)num_sms() * 8 && splits < 64) splits <<= 1;
     const uint32_t min_cols = 1u << 5;   // cbn >= 5 for every array
     if (splits > min_cols) splits = min_cols;
-    k_zero_counts<<<dim3(arrays, splits), 256, 0, s>>>(G, cube, zc, reinterpret_cast<unsigned long long *>(za), splits);
+    k_zero_counts<<<dim3(arrays, splits), 256, 0, s>>>(G, cube, zc, reinterpret_cast<unsigned long long *>(za), splits,
+                                                       cs_lo * G.A);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (eps || zmax) {
-        const uint32_t S = G.smask + 1;
-        k_eps_zmax<<<(S + 127) / 128, 128, 0, s>>>(G, reinterpret_cast<const unsigned long long *>(za), E, eps, zmax);
+        const uint32_t S = cs_hi - cs_lo;
+        k_eps_zmax<<<(S + 127) / 128, 128, 0, s>>>(G, reinterpret_cast<const unsigned long long *>(za), E, eps, zmax,
+                                                   cs_lo, cs_hi);
         e = cudaGetLastError();
     }
     return e;

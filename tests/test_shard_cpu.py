@@ -1,0 +1,85 @@
+"""shard.py's collective steps on CPU with two and four gloo ranks, no GPU.
+
+The sketch exchange must leave in each rank's own slice the OR of every
+rank's copy of that slice, and the host-list gather must return every
+rank's hosts merged by ip.  The OR is injected here as a plain torch
+bitwise OR on CPU tensors (on a GPU it is cbaa_or_words).
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _words(rank, n):
+    rng = np.random.default_rng(100 + rank)
+    return (rng.integers(0, 1 << 32, n, dtype=np.uint64) & rng.integers(0, 1 << 32, n, dtype=np.uint64)) \
+        .astype(np.uint32)
+
+
+def _hosts(rank, k):
+    from paper_1901_06207_b300 import cbaa as C
+    h = np.zeros(k, dtype=C.HOST_DTYPE)
+    h["ip"] = (np.arange(k, dtype=np.uint32) * 7919 + rank) * 4 + rank     # disjoint across ranks
+    h["z"] = rank
+    h["est"] = 1000.0 + rank
+    return h
+
+
+def _rank_main(rank, world, port, words, out):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+    import torch.distributed as dist
+    from paper_1901_06207_b300 import shard
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    mem = torch.from_numpy(_words(rank, words).view(np.int32).copy())
+    recv = torch.empty_like(mem)
+
+    def or_fn(dst, srcs):
+        for s in srcs:
+            dst.bitwise_or_(s)
+
+    own = shard.exchange_slices(mem, rank, world, recv, or_fn)
+    got = shard.gather_hosts(_hosts(rank, 3 + 5 * rank), rank, world, "cpu")
+    out[rank] = (own.numpy().view(np.uint32).copy(), got)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_exchange_and_gather(world):
+    words = 4096
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_rank_main, args=(world, port, words, out), nprocs=world, join=True)
+    per = words // world
+    full = np.zeros(words, dtype=np.uint32)
+    for r in range(world):
+        full |= _words(r, words)
+    want_hosts = np.sort(np.concatenate([_hosts(r, 3 + 5 * r) for r in range(world)]), order="ip")
+    for r in range(world):
+        own, got = out[r]
+        assert np.array_equal(own, full[r * per:(r + 1) * per]), r
+        assert np.array_equal(got, want_hosts), r
+
+
+def test_owned_ranges_partition_the_sketches():
+    from paper_1901_06207_b300 import shard
+    geo = {"r": 5}
+    for world in (1, 2, 4, 8, 16, 32):
+        spans = [shard.owned_range(geo, k, world) for k in range(world)]
+        assert spans[0][0] == 0 and spans[-1][1] == 32
+        assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+    with pytest.raises(ValueError):
+        shard.owned_range(geo, 0, 3)
