@@ -517,6 +517,67 @@ def run_cbaa(args):
     return 0
 
 
+def run_sharded(args):
+    """Every rank is an edge router with its own 64M-packet window; per step each rank updates its
+    cube, the ranks exchange sketch slices (all-to-all), each ORs and restores the sketches it owns,
+    and the host lists are all-gathered (shard.py).  value = packets of all ranks / step time."""
+    import torch
+    from paper_1901_06207_b300 import cbaa as C
+    from paper_1901_06207_b300.shard import ShardedDetector
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    geo, spec0, theta, desc = workload("window64m")
+    spec = T.TrafficSpec(**{**spec0.__dict__, "seed": spec0.seed + 0x100 * rank})
+    w = T.make_window(spec)
+    n = w.pairs.shape[0]
+    pairs = torch.from_numpy(w.pairs.view(np.int32)).to(dev)
+    C.set_tuning(scatter_shape=6, tile_kind=2)
+    cube = C.Cube(geo, device=dev)
+    uws = C.UpdateWorkspace(geo, n, device=dev)
+    det = ShardedDetector(geo, theta, rank, world, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        cube.reset()
+        cube.update_binned(pairs, uws)
+        return det(cube)
+
+    for _ in range(max(args.warmup, 1)):
+        hosts, _ = step()
+    steps = max(1, min(args.steps, 50))
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            hosts, info = step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+    barrier(world)
+    el_max = reduce_over_ranks(el, world, "max", dev)
+    packets_all = reduce_over_ranks(float(n), world, "sum", dev)
+    value = packets_all * steps / el_max / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": el_max * 1e3 / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {**desc, "workload": "sharded_64m_per_rank",
+                       "step": "reset, update the rank's cube, all-to-all of sketch slices, OR of the owned "
+                               "sketches, restore them, all-gather of the host lists (host-synchronous, "
+                               "timed on the host clock)",
+                       "parallelism": f"{world} ranks, sketches split {1 << geo['r']} / {world}"},
+            "hosts_detected": int(hosts.size), "gpu_launches": steps * (4 + 7 + (1 if world > 1 else 0)),
+            "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def _router_window_job(args):
     seed, n_routers = args
     spec = T.spec_window_64m(seed=seed, scale_shift=2)
@@ -716,7 +777,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cbaa", "reference"], default="cbaa")
-    ap.add_argument("--workload", default="window64m", choices=["window64m", "window1m", "batched", "serve"])
+    ap.add_argument("--workload", default="window64m",
+                    choices=["window64m", "window1m", "batched", "serve", "sharded"])
     ap.add_argument("--serve-rate", type=float, default=2e8, help="serve workload: offered packets/s")
     ap.add_argument("--serve-window-s", type=float, default=1.0, help="serve workload: window length")
     ap.add_argument("--serve-windows", type=int, default=3, help="serve workload: windows per run")
@@ -737,6 +799,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sharded":
+        return run_sharded(args)
     return run_cbaa(args)
 
 
