@@ -112,7 +112,8 @@ typedef struct cbaa_detect_info {
 typedef struct cbaa_tuning {
     uint32_t scatter_shape;        /* partitioned update, routing kernel: 0 = 512 threads x 8 packets,
                                       1 = 512 x 4, 2 = 1024 x 4, 3 = 256 x 8, 4 = 256 x 4,
-                                      5 = 1024 x 8, 6 = 512 x 16 */
+                                      5 = 1024 x 8, 6 = 512 x 16, 7 = 256 x 16,
+                                      8 = 1024 x 16 (row tiles; column tiles take 512 x 8) */
     uint32_t count_blocks_per_sm;  /* partitioned update, counting kernel grid (default 8) */
     uint32_t apply_items_per_sm;   /* partitioned update, tile-assembly items per SM (default 8) */
     uint32_t direct_blocks_per_sm; /* direct update grid (default 8 blocks of 256 threads) */

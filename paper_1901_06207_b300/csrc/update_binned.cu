@@ -394,6 +394,8 @@ cudaError_t launch_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uin
         case 4: return launch_scatter<NRA, NVA, 256, 4>(G, S, m, nb, W, s);
         case 5: return launch_scatter<NRA, NVA, 1024, 8>(G, S, m, nb, W, s);
         case 6: return launch_scatter<NRA, NVA, 512, 16>(G, S, m, nb, W, s);
+        case 7: return launch_scatter<NRA, NVA, 256, 16>(G, S, m, nb, W, s);
+        case 8: return launch_scatter<NRA, NVA, 512, 8>(G, S, m, nb, W, s);   // 1024 x 16 exceeds shared memory here
         default: return launch_scatter<NRA, NVA, 512, 8>(G, S, m, nb, W, s);
     }
 }

@@ -260,19 +260,45 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     }
     __syncthreads();
     const uint32_t total = block_exclusive_scan(hist, first, B.nbl, tmp);
-    for (uint32_t b = threadIdx.x; b < B.nbl; b += THREADS) {
-        const uint32_t c = hist[b];
-        if (c) delta[b] = atomicAdd(&cursors[B.global(S, b)], c) - first[b];
-    }
-    __syncthreads();
+    // Run reservations in the record buffer.  Only the copy-out needs them:
+    // with registers to spare (16 packets per thread) the first KB bins'
+    // atomics are issued before the staging and their results wait in
+    // registers, so the staging hides their round trip.
+    constexpr bool EARLY = PPT > 8;
+    constexpr uint32_t KB = EARLY ? 4 : 1;
+    uint32_t base[KB];
+    if (EARLY) {
 #pragma unroll
-    for (uint32_t k = 0; k < PPT; ++k) {
+        for (uint32_t k = 0; k < KB; ++k) {
+            const uint32_t b = threadIdx.x + k * THREADS;
+            const uint32_t c = b < B.nbl ? hist[b] : 0u;
+            base[k] = c ? atomicAdd(&cursors[B.global(S, b)], c) : 0u;
+        }
+    } else {
+        for (uint32_t b = threadIdx.x; b < B.nbl; b += THREADS) {
+            const uint32_t c = hist[b];
+            if (c) delta[b] = atomicAdd(&cursors[B.global(S, b)], c) - first[b];
+        }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < PPT; ++k) {             // first[] is complete after the scan
         if (slot[k] != 0xFFFFFFFFu) {
             const uint32_t b = slot[k] >> 16;
             const uint32_t pos = first[b] + (slot[k] & 0xFFFFu);
             if (SHORT) staged1[pos] = rec[k].x;
             else staged[pos] = rec[k];
             sbin[pos] = b;
+        }
+    }
+    if (EARLY) {
+#pragma unroll
+        for (uint32_t k = 0; k < KB; ++k) {
+            const uint32_t b = threadIdx.x + k * THREADS;
+            if (b < B.nbl && hist[b]) delta[b] = base[k] - first[b];
+        }
+        for (uint32_t b = threadIdx.x + KB * THREADS; b < B.nbl; b += THREADS) {
+            const uint32_t c = hist[b];
+            if (c) delta[b] = atomicAdd(&cursors[B.global(S, b)], c) - first[b];
         }
     }
     __syncthreads();
@@ -415,6 +441,13 @@ cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, 
         case 4: return launch_rt_scatter<256, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
         case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
         case 6: return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        case 7: return launch_rt_scatter<256, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        case 8: {
+            // 1024 x 16 stages 16Ki records: with 8-byte records or many tiles it exceeds shared memory
+            const size_t need = sizeof(uint32_t) * ((((size_t)3 * nb + 1) & ~(size_t)1) + (SHORT ? 2 : 3) * 16384);
+            if (need + 1024 > 227u * 1024u) return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+            return launch_rt_scatter<1024, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        }
         default: return launch_rt_scatter<512, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
     }
 }

@@ -106,7 +106,7 @@ def test_binned_update_passes_ragged_and_incremental(C, oracle):
 
 
 @pytest.mark.parametrize("kind", [1, 2])
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_binned_update_every_scatter_shape(C, oracle, shape, kind):
     """Launch shapes and tilings change timing only: every one gives the oracle's cube."""
     d = GEO.L2
