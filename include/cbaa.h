@@ -118,10 +118,14 @@ typedef struct cbaa_tuning {
     uint32_t apply_items_per_sm;   /* partitioned update, tile-assembly items per SM (default 8) */
     uint32_t direct_blocks_per_sm; /* direct update grid (default 8 blocks of 256 threads) */
     uint32_t tile_kind;            /* partitioned update: 1 = column tiles (128 KiB runs of whole columns,
-                                      one routed code per bit), 2 = row tiles (one row word of every column
-                                      of a sketch, one routed record per packet; only where the geometry
-                                      allows: sketch words / W <= 32768 and tiles <= 8192), 0 = row tiles
-                                      where allowed, else column tiles */
+                                      one routed code per bit); row tiles (one row word of every column of
+                                      a sketch, one routed record per packet; only where the geometry
+                                      allows: sketch words / W <= 32768 and tiles <= 8192) with
+                                      2 = run sizes from counting every packet, 3 = run capacities from
+                                      counting every 16th tile of 1024 packets (records past a capacity
+                                      are set by direct reductions; needs workspace room for an overflow
+                                      list of every packet, else 2); 0 = 3 for passes of >= 8Mi packets,
+                                      2 below, column tiles where row tiles are not allowed */
 } cbaa_tuning;
 
 typedef struct cbaa_cube cbaa_cube;   /* opaque handle: a params copy plus the caller's memory */

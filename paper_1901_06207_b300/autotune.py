@@ -27,7 +27,7 @@ def _key(geo: dict, n: int, device_name: str) -> str:
 def candidates():
     for b in (4, 8, 16, 32):
         yield "direct", dict(direct_blocks_per_sm=b)
-    for kind, shape, items, cnt in itertools.product((1, 2), range(9), (4, 8, 16), (4, 8)):
+    for kind, shape, items, cnt in itertools.product((1, 2, 3), range(9), (4, 8, 16), (4, 8)):
         yield "binned", dict(tile_kind=kind, scatter_shape=shape, apply_items_per_sm=items, count_blocks_per_sm=cnt)
 
 

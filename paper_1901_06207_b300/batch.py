@@ -87,7 +87,7 @@ class RouterWindows:
         stream = torch.cuda.current_stream()
         best = None
         base = C.get_tuning()
-        for kind in (1, 2):
+        for kind in (1, 2, 3):
             C.set_tuning(**{**base, "tile_kind": kind})
             times = []
             for rep in range(reps + 1):

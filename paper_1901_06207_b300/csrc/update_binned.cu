@@ -207,10 +207,17 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(const Geo G, const 
 
 // One block: offsets = exclusive scan of counts, cursors = offsets,
 // items = exclusive scan of ceil(counts / ch) (item_start[nb] = total).
-__global__ void __launch_bounds__(1024) k_bin_scan(const uint32_t *__restrict__ counts, uint32_t nb, uint32_t ch,
+// samp > 1: counts are those of a 1-in-samp sample of the packets and are
+// first replaced by run capacities (sample_capacity).
+__global__ void __launch_bounds__(1024) k_bin_scan(uint32_t *__restrict__ counts, uint32_t nb, uint32_t ch,
                                                    uint32_t *__restrict__ offsets, uint32_t *__restrict__ cursors,
-                                                   uint32_t *__restrict__ item_start, uint32_t *__restrict__ nchunk) {
+                                                   uint32_t *__restrict__ item_start, uint32_t *__restrict__ nchunk,
+                                                   uint32_t samp) {
     __shared__ uint32_t tmp[32];
+    if (samp > 1) {
+        for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) counts[i] = sample_capacity(counts[i], samp);
+        __syncthreads();
+    }
     const uint32_t total = block_exclusive_scan(counts, offsets, nb, tmp);
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
         cursors[i] = offsets[i];
@@ -435,7 +442,7 @@ cudaError_t launch_binned_t(const Geo &G, const BinSegs &S0, uint64_t n, const B
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         uint64_t ch = ((uint64_t)A * m + (uint64_t)sms * apply_ips - 1) / ((uint64_t)sms * apply_ips);
         if (ch < (1u << 14)) ch = 1u << 14;
-        k_bin_scan<<<1, 1024, 0, s>>>(W.counts, nb, (uint32_t)ch, W.offsets, W.cursors, W.item_start, W.nchunk);
+        k_bin_scan<<<1, 1024, 0, s>>>(W.counts, nb, (uint32_t)ch, W.offsets, W.cursors, W.item_start, W.nchunk, 1u);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = launch_scatter_shape<NRA, NVA>(G, S, m, nb, W, T.scatter_shape, s)) != cudaSuccess) return e;
         k_bin_apply<<<(unsigned)sms, kApplyThreads, apply_smem, s>>>(S, G.cube_words, W.codes, W.offsets,
@@ -448,8 +455,9 @@ cudaError_t launch_binned_t(const Geo &G, const BinSegs &S0, uint64_t n, const B
 
 }  // namespace
 
-cudaError_t launch_bin_scan(const uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s) {
-    k_bin_scan<<<1, 1024, 0, s>>>(counts, nb, ch, W.offsets, W.cursors, W.item_start, W.nchunk);
+cudaError_t launch_bin_scan(uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s,
+                            uint32_t samp) {
+    k_bin_scan<<<1, 1024, 0, s>>>(counts, nb, ch, W.offsets, W.cursors, W.item_start, W.nchunk, samp);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Partitioned (binned) update: tile-space description, workspace, launch.
 #pragma once
 
+#include <cmath>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -83,6 +84,32 @@ cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, c
                                    cudaStream_t s);
 cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                                   cudaStream_t s);
-cudaError_t launch_bin_scan(const uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s);
+cudaError_t launch_bin_scan(uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s,
+                            uint32_t samp = 1);
+
+// Run capacity of a tile from its count c in a 1-in-samp sample of the
+// packets: the estimate c*samp, plus 1/8 of it, plus four standard
+// deviations of the sampled estimate (samp*sqrt(c+1)), plus 256.  Only
+// time depends on it: records beyond a run's capacity take the overflow
+// path.  sample_capacity_bound() bounds the sum over all tiles.
+__host__ __device__ inline uint32_t sample_capacity(uint32_t c, uint32_t samp) {
+    const uint64_t est = (uint64_t)c * samp;
+    const uint64_t c1 = (uint64_t)c + 1;                  // r = ceil(sqrt(c + 1)), exact
+    uint32_t r = (uint32_t)sqrtf((float)c1);
+    while ((uint64_t)r * r < c1) ++r;
+    while (r > 1 && (uint64_t)(r - 1) * (r - 1) >= c1) --r;
+    const uint64_t cap = est + est / 8 + 4ull * samp * r + 256;
+    return cap > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap;
+}
+
+// Upper bound of sum_b sample_capacity(c_b, samp) when m packets are
+// sampled in tiles of `tile` (sum_b c_b <= m/samp + tile): the estimates sum
+// to at most m + samp*tile, and sum_b sqrt(c_b + 1) <= sqrt(nb * sum(c_b + 1))
+// (Cauchy-Schwarz), plus one per tile for the ceiling.
+inline uint64_t sample_capacity_bound(uint64_t m, uint32_t nb, uint32_t samp, uint32_t tile) {
+    const uint64_t est = m + (uint64_t)samp * tile;
+    const double rt = std::sqrt((double)nb * ((double)est / samp + (double)tile + nb)) + nb;
+    return est + est / 8 + (uint64_t)(4.0 * samp * rt) + 4ull * samp + 257ull * nb;
+}
 
 }  // namespace cbaa

@@ -26,7 +26,6 @@
 
 namespace cbaa {
 
-cudaError_t launch_bin_scan(const uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s);
 
 namespace {
 
@@ -136,21 +135,23 @@ constexpr uint32_t kCountTile = 4 * kCountThreads;
 
 // ORIENT (the cube has an inner network): packets are raw {src, dst} (orient()).
 template <bool MULTI, bool ORIENT>
+// samp > 1: only every samp-th tile of kCountTile packets is counted (a
+// sample for run capacities, see sample_capacity).
 __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
-                                                            uint32_t *__restrict__ counts) {
+                                                            uint32_t *__restrict__ counts, uint32_t samp) {
     extern __shared__ uint32_t hist[];
     uint64_t lo, hi, step;
     if (MULTI) {
         const uint64_t tiles = (n + kCountTile - 1) / kCountTile;
-        const uint64_t chunk = (tiles + gridDim.x - 1) / gridDim.x * kCountTile;
-        lo = (uint64_t)blockIdx.x * chunk;
+        const uint64_t per = ((tiles + gridDim.x - 1) / gridDim.x + samp - 1) / samp * samp;
+        lo = (uint64_t)blockIdx.x * per * kCountTile;
         if (lo >= n) return;                               // the whole block leaves before any barrier
-        hi = lo + chunk < n ? lo + chunk : n;
-        step = kCountTile;
+        hi = lo + per * kCountTile < n ? lo + per * kCountTile : n;
+        step = (uint64_t)kCountTile * samp;
     } else {
-        lo = (uint64_t)blockIdx.x * kCountTile;
+        lo = (uint64_t)blockIdx.x * kCountTile * samp;
         hi = n;
-        step = (uint64_t)gridDim.x * kCountTile;
+        step = (uint64_t)gridDim.x * kCountTile * samp;
     }
     BlockTiles B;
     if (MULTI) {
@@ -195,7 +196,9 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
 // records: 2048 threads per SM, measured ~8 % faster) or 42 (8-byte records).
 template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT>
 __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) / THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
-                                                        uint32_t *__restrict__ cursors, void *__restrict__ recs_out) {
+                                                        uint32_t *__restrict__ cursors, void *__restrict__ recs_out,
+                                                        const uint32_t *__restrict__ offsets, uint2 *__restrict__ ovf,
+                                                        uint32_t *__restrict__ ovf_count, uint32_t ovf_cap) {
     extern __shared__ uint32_t sm[];
     uint32_t *hist = sm;
     uint32_t *first = sm + nb;     // exclusive start of each tile's run in `staged`
@@ -267,6 +270,18 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     constexpr bool EARLY = PPT > 8;
     constexpr uint32_t KB = EARLY ? 4 : 1;
     uint32_t base[KB];
+    // A run reserved at `at`: delta maps staging positions to the record
+    // buffer.  With sampled capacities (ovf set) hist[b] becomes the end, in
+    // staging positions, of the part of the run that fits before its tile's
+    // capacity ends; the rest overflows.
+    auto reserved = [&](uint32_t b, uint32_t c, uint32_t at) {
+        delta[b] = at - first[b];
+        if (ovf) {
+            const uint32_t end = offsets[B.global(S, b) + 1];
+            const uint32_t room = end > at ? end - at : 0u;
+            hist[b] = first[b] + (c < room ? c : room);
+        }
+    };
     if (EARLY) {
 #pragma unroll
         for (uint32_t k = 0; k < KB; ++k) {
@@ -277,7 +292,7 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     } else {
         for (uint32_t b = threadIdx.x; b < B.nbl; b += THREADS) {
             const uint32_t c = hist[b];
-            if (c) delta[b] = atomicAdd(&cursors[B.global(S, b)], c) - first[b];
+            if (c) reserved(b, c, atomicAdd(&cursors[B.global(S, b)], c));
         }
     }
 #pragma unroll
@@ -294,20 +309,41 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
 #pragma unroll
         for (uint32_t k = 0; k < KB; ++k) {
             const uint32_t b = threadIdx.x + k * THREADS;
-            if (b < B.nbl && hist[b]) delta[b] = base[k] - first[b];
+            if (b < B.nbl) {
+                const uint32_t c = hist[b];
+                if (c) reserved(b, c, base[k]);
+            }
         }
         for (uint32_t b = threadIdx.x + KB * THREADS; b < B.nbl; b += THREADS) {
             const uint32_t c = hist[b];
-            if (c) delta[b] = atomicAdd(&cursors[B.global(S, b)], c) - first[b];
+            if (c) reserved(b, c, atomicAdd(&cursors[B.global(S, b)], c));
         }
     }
     __syncthreads();
-    if (SHORT) {
-        uint32_t *recs = static_cast<uint32_t *>(recs_out);
-        for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged1[t];
-    } else {
-        uint2 *recs = static_cast<uint2 *>(recs_out);
-        for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged[t];
+    if (!ovf) {
+        if (SHORT) {
+            uint32_t *recs = static_cast<uint32_t *>(recs_out);
+            for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged1[t];
+        } else {
+            uint2 *recs = static_cast<uint2 *>(recs_out);
+            for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged[t];
+        }
+        return;
+    }
+    // sampled capacities: records past their run's capacity go to the overflow list as
+    // {record, tile} (4-byte records) or {mangled ip, row | cube << 16}
+    for (uint32_t t = threadIdx.x; t < total; t += THREADS) {
+        const uint32_t b = sbin[t];
+        if (t < hist[b]) {
+            if (SHORT) static_cast<uint32_t *>(recs_out)[delta[b] + t] = staged1[t];
+            else static_cast<uint2 *>(recs_out)[delta[b] + t] = staged[t];
+        } else {
+            const uint32_t gb = B.global(S, b);
+            const uint2 e = SHORT ? make_uint2(staged1[t], gb)
+                                  : make_uint2(staged[t].x, staged[t].y | ((gb / B.tpr) << 16));
+            const uint32_t at = atomicAdd(ovf_count, 1u);
+            if (at < ovf_cap) ovf[at] = e;
+        }
     }
 }
 
@@ -346,7 +382,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
                                                             const uint32_t *__restrict__ offsets,
                                                             const uint32_t *__restrict__ item_start, uint32_t nb,
                                                             uint32_t ch, uint32_t tile_words,
-                                                            uint32_t *__restrict__ queue) {
+                                                            uint32_t *__restrict__ queue,
+                                                            const uint32_t *__restrict__ cursors) {
     extern __shared__ uint32_t tile[];
     __shared__ uint32_t s_item;
     const uint32_t items = item_start[nb];
@@ -363,8 +400,13 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
         }
         const uint32_t b = lo;
         const uint32_t c0 = offsets[b] + (item - item_start[b]) * ch;
-        const uint32_t cend = offsets[b + 1];
+        // records written: up to the run's end, or fewer when its capacity came from a sample
+        const uint32_t cend = offsets[b + 1] < cursors[b] ? offsets[b + 1] : cursors[b];
         const uint32_t c1 = c0 + ch < cend ? c0 + ch : cend;
+        if (c0 >= c1) {                                   // an empty item (sampled capacities)
+            __syncthreads();                              // s_item is read by every thread first
+            continue;
+        }
         for (uint32_t i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0;
         __syncthreads();
         uint32_t c = c0 + threadIdx.x;
@@ -390,6 +432,41 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
             red_or(cube + G.arr_base[a] + (size_t)col * G.W, v);
         }
         __syncthreads();
+    }
+}
+
+// Records of a sampled pass that did not fit their run's capacity: each sets
+// its |RA|+|VA| bits straight in the cube (one L2 reduction per bit, as the
+// direct update does).  The count is read on the device, so a pass without
+// overflow costs one short launch.
+template <bool SHORT>
+__global__ void __launch_bounds__(256) k_rt_overflow(const Geo G, const BinSegs S, const uint2 *__restrict__ ovf,
+                                                     const uint32_t *__restrict__ ovf_count, uint32_t cap) {
+    const uint32_t n = *ovf_count < cap ? *ovf_count : cap;
+    const uint32_t tpr = (G.smask + 1) * G.W;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint2 e = ovf[i];
+        uint32_t lp, bit, router, cs, w;
+        if (SHORT) {
+            lp = e.x >> 5;
+            bit = e.x & 31u;
+            router = e.y / tpr;
+            const uint32_t rem = e.y - router * tpr;
+            cs = rem / G.W;
+            w = rem - cs * G.W;
+        } else {
+            const uint32_t row = e.y & 0xFFFFu;
+            router = e.y >> 16;
+            cs = e.x & G.smask;
+            lp = e.x >> G.r;
+            w = row >> 5;
+            bit = row & 31u;
+        }
+        uint32_t *base = S.cube[router] + (size_t)cs * G.cs_words + w;
+        for (uint32_t a = 0; a < G.A; ++a) {
+            const uint32_t col = a < G.n_ra ? ra_col(G, a, lp) : va_col(G, a - G.n_ra, lp);
+            red_or(base + G.arr_base[a] + (size_t)col * G.W, 1u << bit);
+        }
     }
 }
 
@@ -419,44 +496,52 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaSuccess;
 }
 
+// Overflow list of a sampled pass (null: exact counts, no overflow).
+struct Overflow {
+    uint2 *list;
+    uint32_t *count;
+    uint32_t cap;
+};
+
 template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT>
 cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
-                              cudaStream_t s) {
+                              const Overflow &O, cudaStream_t s) {
     const size_t per = SHORT ? 2 : 3;                 // staged record words + bin word per packet
     const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nb + 1) & ~(size_t)1) + per * THREADS * PPT);
     cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT>, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
-    k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes);
+    k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes,
+                                                                                W.offsets, O.list, O.count, O.cap);
     return cudaGetLastError();
 }
 
 template <bool SHORT, bool MULTI, bool ORIENT>
 cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
-                                    uint32_t shape, cudaStream_t s) {
+                                    const Overflow &O, uint32_t shape, cudaStream_t s) {
     switch (shape) {
-        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
-        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
-        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
-        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
-        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
-        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
-        case 7: return launch_rt_scatter<256, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+        case 7: return launch_rt_scatter<256, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
         case 8: {
             // 1024 x 16 stages 16Ki records: with 8-byte records or many tiles it exceeds shared memory
             const size_t need = sizeof(uint32_t) * ((((size_t)3 * nb + 1) & ~(size_t)1) + (SHORT ? 2 : 3) * 16384);
-            if (need + 1024 > 227u * 1024u) return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
-            return launch_rt_scatter<1024, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+            if (need + 1024 > 227u * 1024u) return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+            return launch_rt_scatter<1024, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
         }
-        default: return launch_rt_scatter<512, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, s);
+        default: return launch_rt_scatter<512, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
     }
 }
 
 template <bool MULTI, bool ORIENT>
 cudaError_t launch_rt_scatter_kind(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
-                                   uint32_t shape, cudaStream_t s) {
-    return G.r >= 5 ? launch_rt_scatter_shape<true, MULTI, ORIENT>(G, S, m, nb, W, shape, s)
-                    : launch_rt_scatter_shape<false, MULTI, ORIENT>(G, S, m, nb, W, shape, s);
+                                   const Overflow &O, uint32_t shape, cudaStream_t s) {
+    return G.r >= 5 ? launch_rt_scatter_shape<true, MULTI, ORIENT>(G, S, m, nb, W, O, shape, s)
+                    : launch_rt_scatter_shape<false, MULTI, ORIENT>(G, S, m, nb, W, O, shape, s);
 }
 
 template <typename Rec>
@@ -471,7 +556,8 @@ cudaError_t launch_rt_apply(const Geo &G, const BinSegs &S, const BinWs &W, uint
         per_sm < 1)
         per_sm = 1;
     kapply<<<(unsigned)(sms * per_sm), kApplyThreads, smem, s>>>(G, S, reinterpret_cast<const Rec *>(W.codes),
-                                                                 W.offsets, W.item_start, nb, ch, tw, W.nchunk + nb);
+                                                                 W.offsets, W.item_start, nb, ch, tw, W.nchunk + nb,
+                                                                 W.cursors);
     return cudaGetLastError();
 }
 
@@ -479,6 +565,27 @@ cudaError_t launch_rt_apply(const Geo &G, const BinSegs &S, const BinWs &W, uint
 
 uint32_t rowtile_bins(const Geo &G, uint32_t n_cubes) { return n_cubes * (G.smask + 1) * G.W; }
 uint32_t rowtile_words(const Geo &G) { return G.col_base[G.A]; }
+
+constexpr uint32_t kSample = 16;                  // sampled passes count 1 tile in 16
+constexpr uint64_t kMinSampled = 8ull << 20;      // below this every packet is counted
+
+// Words of a sampled pass of m packets: records up to the capacity bound,
+// then an overflow list with room for every packet.
+static uint64_t sampled_words(uint64_t m, uint32_t nb, uint64_t rec_words) {
+    return ((rec_words * sample_capacity_bound(m, nb, kSample, kCountTile) + 3) & ~3ull) + 2 * m + 8;
+}
+
+// Largest sampled pass (at most `want` packets) that fits the workspace.
+static uint64_t sampled_pass_max(const Geo &G, const BinWs &W, uint32_t nb, uint64_t rec_words, uint64_t want) {
+    const uint64_t cap_words = (uint64_t)W.max_pairs * G.A;
+    if (sampled_words(want, nb, rec_words) <= cap_words) return want;
+    uint64_t lo = 0, hi = want;
+    while (hi - lo > 1) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (sampled_words(mid, nb, rec_words) <= cap_words) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                                   cudaStream_t s) {
@@ -497,8 +604,20 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
     const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
     const uint32_t apply_ips = T.apply_items_per_sm ? T.apply_items_per_sm : 8;
     const uint64_t max_pairs = W.max_pairs * G.A / rec_words;   // the buffer holds A words per packet
+    // tile_kind 3: run capacities from a 1-in-16 sample of the packets (records
+    // past a capacity take the overflow path), where the workspace allows it
+    // tile_kind 0 (the default) samples passes of at least kMinSampled packets
+    uint64_t max_sampled = 0;
+    if (T.tile_kind == 3 || (T.tile_kind == 0 && n >= kMinSampled)) {
+        max_sampled = sampled_pass_max(G, W, nb, rec_words, n);
+        const uint64_t least = T.tile_kind == 3 ? (n < (1u << 16) ? n : (1u << 16)) : kMinSampled;
+        if (max_sampled < least) max_sampled = 0;
+    }
+    const bool sampled = max_sampled > 0;
+    const uint32_t samp = sampled ? kSample : 1u;
     for (uint64_t done = 0; done < n;) {
-        const uint64_t m = (n - done) < max_pairs ? (n - done) : max_pairs;
+        const uint64_t lim = sampled ? max_sampled : max_pairs;
+        const uint64_t m = (n - done) < lim ? (n - done) : lim;
         BinSegs S = S0;
         S.k = 0;
         for (uint32_t j = 0; j < S0.k; ++j) {
@@ -511,26 +630,37 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
             ++S.k;
         }
         S.start[S.k] = m;
-        if ((e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * nb, s)) != cudaSuccess) return e;
-        const uint64_t want = (m + kCountTile - 1) / kCountTile;
+        // counts[nb] is the overflow counter of a sampled pass
+        if ((e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * (nb + 1), s)) != cudaSuccess) return e;
+        const uint64_t want = (m + (uint64_t)kCountTile * samp - 1) / ((uint64_t)kCountTile * samp);
         const uint64_t cap = (uint64_t)sms * count_bps;
         const unsigned cgrid = (unsigned)(want < cap ? want : cap);
-        kcount<<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts);
+        kcount<<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts, samp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // split a row tile only when it holds more than apply_ips/2 times the average tile
         uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
         if (ch < (1u << 12)) ch = 1u << 12;
-        if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s)) != cudaSuccess) return e;
+        if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s, samp)) != cudaSuccess) return e;
+        Overflow O{nullptr, nullptr, 0};
+        if (sampled) {
+            const uint64_t rec_region = (rec_words * sample_capacity_bound(m, nb, kSample, kCountTile) + 3) & ~3ull;
+            O = Overflow{reinterpret_cast<uint2 *>(W.codes + rec_region), W.counts + nb, (uint32_t)m};
+        }
         if (multi)
-            e = ori ? launch_rt_scatter_kind<true, true>(G, S, m, nb, W, T.scatter_shape, s)
-                    : launch_rt_scatter_kind<true, false>(G, S, m, nb, W, T.scatter_shape, s);
+            e = ori ? launch_rt_scatter_kind<true, true>(G, S, m, nb, W, O, T.scatter_shape, s)
+                    : launch_rt_scatter_kind<true, false>(G, S, m, nb, W, O, T.scatter_shape, s);
         else
-            e = ori ? launch_rt_scatter_kind<false, true>(G, S, m, nb, W, T.scatter_shape, s)
-                    : launch_rt_scatter_kind<false, false>(G, S, m, nb, W, T.scatter_shape, s);
+            e = ori ? launch_rt_scatter_kind<false, true>(G, S, m, nb, W, O, T.scatter_shape, s)
+                    : launch_rt_scatter_kind<false, false>(G, S, m, nb, W, O, T.scatter_shape, s);
         if (e != cudaSuccess) return e;
         e = short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s)
                       : launch_rt_apply<uint2>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s);
         if (e != cudaSuccess) return e;
+        if (sampled) {
+            if (short_rec) k_rt_overflow<true><<<(unsigned)sms * 2, 256, 0, s>>>(G, S, O.list, O.count, O.cap);
+            else k_rt_overflow<false><<<(unsigned)sms * 2, 256, 0, s>>>(G, S, O.list, O.count, O.cap);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         done += m;
     }
     return cudaSuccess;

@@ -117,7 +117,7 @@ def test_tuning_roundtrip_and_limits(C):
     assert C.get_tuning() == dict(scatter_shape=3, count_blocks_per_sm=4, apply_items_per_sm=16,
                                   direct_blocks_per_sm=2, tile_kind=1)
     with pytest.raises(C.CbaaError):
-        C.set_tuning(tile_kind=3)
+        C.set_tuning(tile_kind=4)
     with pytest.raises(C.CbaaError):
         C.set_tuning(scatter_shape=9)
     C.set_tuning(**before)

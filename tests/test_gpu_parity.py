@@ -105,7 +105,7 @@ def test_binned_update_passes_ragged_and_incremental(C, oracle):
     assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_binned_update_every_scatter_shape(C, oracle, shape, kind):
     """Launch shapes and tilings change timing only: every one gives the oracle's cube."""
@@ -122,7 +122,7 @@ def test_binned_update_every_scatter_shape(C, oracle, shape, kind):
         C.set_tuning(**before)
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 @pytest.mark.parametrize("geo,win,k", [("TINY2", "tiny", 5), ("L2", "4m", 8), ("TINY", "tiny", 16),
                                        ("PAPER", "1m", 2), ("SERVE", "4m", 1)])
 def test_multi_router_update(C, oracle, geo, win, k, kind):
@@ -150,7 +150,7 @@ def _multi_router_case(C, oracle, geo, win, k):
     assert np.array_equal(glob.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 @pytest.mark.parametrize("geo", ["L2", "PAPER"])
 def test_binned_update_skewed_runs(C, oracle, geo, kind):
     """Half the packets one pair, a fifth one source to many peers: a few tiles take most of
@@ -169,6 +169,36 @@ def test_binned_update_skewed_runs(C, oracle, geo, kind):
         cube = C.Cube(d)
         cube.update_binned(dev_pairs(pairs), C.UpdateWorkspace(d, n))
         assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, pairs))
+    finally:
+        C.set_tuning(**before)
+
+
+@pytest.mark.parametrize("geo,routers", [("L2", 1), ("L2", 3), ("PAPER", 1)])
+def test_sampled_capacities_overflow(C, oracle, geo, routers):
+    """tile_kind 3 sizes each tile's run from every 16th tile of 1024 packets.  Here one source
+    sends half of the packets, but only in the tiles the sample skips, so its tiles get runs sized
+    for background traffic and tens of thousands of records overflow: the overflow path must
+    still give the oracle's cubes."""
+    d = GEO.ALL[geo]
+    rng = np.random.default_rng(21)
+    n = 1 << 21
+    pairs = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    hot = ((np.arange(n) // 1024) % 16 != 0) & (rng.random(n) < 0.5)
+    pairs[hot, 0] = 0x0D0E0A0F
+    before = C.get_tuning()
+    try:
+        C.set_tuning(**{**before, "tile_kind": 3})
+        if routers == 1:
+            cube = C.Cube(d)
+            cube.update_binned(dev_pairs(pairs), C.UpdateWorkspace(d, n))
+            assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, pairs))
+        else:
+            cut = np.linspace(0, n, routers + 1).astype(int)
+            cubes = [C.Cube(d) for _ in range(routers)]
+            C.update_multi(cubes, [dev_pairs(pairs[cut[j]:cut[j + 1]]) for j in range(routers)],
+                           C.UpdateWorkspace(d, n, n_cubes=routers))
+            for j in range(routers):
+                assert np.array_equal(cubes[j].to_numpy(), oracle.build_cube(d, pairs[cut[j]:cut[j + 1]])), j
     finally:
         C.set_tuning(**before)
 
