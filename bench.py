@@ -270,7 +270,9 @@ def run_cbaa(args):
         tuned = autotune.tune_update(geo, pairs_dev, device=dev, use_cache=False)
         path = tuned["path"]
     else:
-        tuned, path = None, args.update            # library default shapes
+        tuned, path = None, args.update            # library default shapes, or --tuning
+        if args.tuning:
+            C.set_tuning(**json.loads(args.tuning))
     uws = C.UpdateWorkspace(geo, n, device=dev) if path == "binned" else None
     cap = 1 << 16
     out = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
@@ -785,6 +787,8 @@ def main():
     ap.add_argument("--update", default="auto", choices=["auto", "binned", "direct"],
                     help="Alg. 1 path: partitioned by cube tile (binned), RED.OR into the cube (direct), "
                          "or the autotuner's pick (auto)")
+    ap.add_argument("--tuning", default="", help="with --update binned/direct: launch shapes as JSON, e.g. "
+                                                 "'{\"scatter_shape\": 6, \"tile_kind\": 3}'")
     ap.add_argument("--windows", type=int, default=16, help="batched workload: windows per batch")
     ap.add_argument("--routers", type=int, default=8, help="batched workload: simulated edge routers")
     ap.add_argument("--reference-sample", type=int, default=4 << 20,
