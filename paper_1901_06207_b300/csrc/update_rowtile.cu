@@ -274,12 +274,14 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     // buffer.  With sampled capacities (ovf set) hist[b] becomes the end, in
     // staging positions, of the part of the run that fits before its tile's
     // capacity ends; the rest overflows.
+    bool spill = false;                               // some record of this thread's bins overflows
     auto reserved = [&](uint32_t b, uint32_t c, uint32_t at) {
         delta[b] = at - first[b];
         if (ovf) {
             const uint32_t end = offsets[B.global(S, b) + 1];
             const uint32_t room = end > at ? end - at : 0u;
             hist[b] = first[b] + (c < room ? c : room);
+            spill |= room < c;
         }
     };
     if (EARLY) {
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
             if (c) reserved(b, c, atomicAdd(&cursors[B.global(S, b)], c));
         }
     }
-    __syncthreads();
-    if (!ovf) {
+    const bool any_spill = __syncthreads_or(spill);
+    if (!any_spill) {                                 // nothing overflows: the plain copy-out
         if (SHORT) {
             uint32_t *recs = static_cast<uint32_t *>(recs_out);
             for (uint32_t t = threadIdx.x; t < total; t += THREADS) recs[delta[sbin[t]] + t] = staged1[t];
