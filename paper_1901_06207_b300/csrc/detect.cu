@@ -46,42 +46,63 @@ __global__ void __launch_bounds__(1024) k_hot_lists(const Geo G, WsPtrs P, uint3
     const uint16_t *zc = P.zc + ((size_t)cs * G.A + i) * G.cmax;
     uint16_t *list = P.hc + ((size_t)cs * G.n_ra + i) * P.hc_stride;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    constexpr uint32_t CPT = 4;                       // list positions p per thread and chunk
 
-    __shared__ uint32_t warp_tot[32], warp_off[32], s_base, s_count;
+    __shared__ uint32_t warp_tot[32], s_base, s_count;
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
 
-    for (uint32_t p0 = 0; p0 < ncol; p0 += blockDim.x) {
-        const uint32_t p = p0 + threadIdx.x;
-        uint32_t col = 0;
-        bool hot = false;
-        if (p < ncol) {
-            col = ((p & ((1u << jb) - 1u)) << kb) | (p >> jb);
-            hot = (int64_t)zc[col] <= zm;
+    // list position p holds column ((p mod 2^jb) << kb) | (p >> jb): key-major order
+    for (uint32_t p0 = 0; p0 < ncol; p0 += CPT * blockDim.x) {
+        uint32_t col[CPT], mine = 0, flags = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < CPT; ++j) {
+            const uint32_t p = p0 + CPT * threadIdx.x + j;
+            col[j] = 0;
+            if (p < ncol) {
+                col[j] = ((p & ((1u << jb) - 1u)) << kb) | (p >> jb);
+                if ((int64_t)zc[col[j]] <= zm) {
+                    flags |= 1u << j;
+                    ++mine;
+                }
+            }
         }
-        const uint32_t b = __ballot_sync(0xffffffffu, hot);
-        if (lane == 0) warp_tot[warp] = __popc(b);
+        uint32_t x = mine;                            // exclusive position of this thread's hot columns
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t run = 0;
-            for (uint32_t w = 0; w < blockDim.x / 32; ++w) { warp_off[w] = run; run += warp_tot[w]; }
-            s_base = s_count;
-            s_count += run;
-            if (i == 0 && run > 0) s_base = atomicAdd(&P.state->stage_count[0], run);
+        if (warp == 0) {
+            uint32_t v = lane < blockDim.x / 32 ? warp_tot[lane] : 0u;
+            for (uint32_t o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            warp_tot[lane] = v;                       // inclusive over warps
+            if (lane == 31) {
+                s_base = s_count;
+                s_count += v;
+                if (i == 0 && v > 0) s_base = atomicAdd(&P.state->stage_count[0], v);
+            }
         }
         __syncthreads();
-        if (hot) {
-            const uint32_t pos = s_base + warp_off[warp] + __popc(b & ((1u << lane) - 1u));
+        uint32_t pos = s_base + (warp ? warp_tot[warp - 1] : 0u) + x - mine;
+#pragma unroll
+        for (uint32_t j = 0; j < CPT; ++j) {
+            if (!(flags >> j & 1u)) continue;
             if (i == 0) {
                 if (pos < P.m) {
                     Tuple t;
                     t.cs = (uint16_t)cs;
-                    t.hc[0] = (uint16_t)col;
+                    t.hc[0] = (uint16_t)col[j];
                     P.tup[0][pos] = t;
                 }
             } else {
-                list[pos] = (uint16_t)col;
+                list[pos] = (uint16_t)col[j];
             }
+            ++pos;
         }
         __syncthreads();
     }

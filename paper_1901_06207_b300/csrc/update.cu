@@ -110,9 +110,17 @@ __global__ void __launch_bounds__(256) k_merge(uint4 *__restrict__ dst, const Sr
 
 // ---------------------------------------------------------------------------
 // Zero counts.  Block (cs*A + a, split) walks a slice of array a of sketch
-// cs; TPC threads share one column (TPC = min(W/4, 32)), each summing the
-// popcounts of its 16-byte pieces, then the TPC lanes reduce by shuffles.
-// One atomic per block adds the slice's zeros to za[cs][a].
+// cs.  TPC threads share one column, each summing the popcounts of its
+// PER 16-byte pieces (TPC = W/(4 ZC_PIECES) clamped to [1, 32], so a
+// thread has ZC_PIECES pieces of a column when the column is long enough),
+// then the TPC lanes reduce by shuffles.  ZC_U columns per thread group are
+// in flight.  One atomic per block adds the slice's zeros to za[cs][a].
+#ifndef ZC_PIECES
+#define ZC_PIECES 4
+#endif
+#ifndef ZC_U
+#define ZC_U 2
+#endif
 
 __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t *__restrict__ cube,
                                                      uint16_t *__restrict__ zc,
@@ -124,14 +132,15 @@ __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t
     const uint32_t c0 = (uint32_t)(((uint64_t)ncol * blockIdx.y) / splits);
     const uint32_t c1 = (uint32_t)(((uint64_t)ncol * (blockIdx.y + 1)) / splits);
     const uint32_t q = G.W / 4;                      // 16-byte pieces per column
-    const uint32_t tpc = q < 32 ? q : 32;
+    const uint32_t t0 = q / ZC_PIECES;
+    const uint32_t tpc = t0 < 1 ? 1 : (t0 > 32 ? 32 : t0);
     const uint32_t per = q / tpc;                    // pieces per thread
     const uint32_t sub = threadIdx.x % tpc;
     const uint32_t cols_per_iter = blockDim.x / tpc;
     const uint4 *arr4 = reinterpret_cast<const uint4 *>(cube + (size_t)cs * G.cs_words + G.arr_base[a]);
 
     unsigned long long acc = 0;
-    constexpr uint32_t U = 4;                        // columns in flight per thread group
+    constexpr uint32_t U = ZC_U;
     for (uint32_t base = c0; base < c1; base += U * cols_per_iter) {
         uint32_t ones[U];
 #pragma unroll
@@ -139,9 +148,10 @@ __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t
             const uint32_t col = base + u * cols_per_iter + threadIdx.x / tpc;
             ones[u] = 0;
             if (col < c1) {
-                const uint4 *c4 = arr4 + (size_t)col * q;
+                const uint4 *c4 = arr4 + (size_t)col * q + sub;
+#pragma unroll 4
                 for (uint32_t k = 0; k < per; ++k) {
-                    const uint4 v = c4[sub + k * tpc];
+                    const uint4 v = c4[k * tpc];
                     ones[u] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
                 }
             }
