@@ -202,78 +202,88 @@ __global__ void __launch_bounds__(256) k_join(const Geo G, const uint32_t *__res
             for (uint32_t i = 0; i < s; ++i) lp_part |= ((uint32_t)tu.hc[i] & ((1u << G.ep[i]) - 1u)) << G.ring_off[i];
         const uint32_t close_bits = (uint32_t)tu.hc[0] & ((1u << G.cp[s]) - 1u);
 
-        // U candidates per iteration: their list entries, then all their column
-        // loads (and, in the last stage, the VA columns, which need only the
-        // list entry), then the U reductions.  ok[u] is the same in every lane.
+        // The bucket is read 32 entries at a time, one per lane, with the ring
+        // closure (Alg. 3 step 1, last stage) tested in every lane at once; the
+        // surviving candidates are taken U at a time: all their column loads
+        // (and, in the last stage, the VA columns, which need only the list
+        // entry), then the U reductions.  pending and ok[u] are the same in
+        // every lane.
         constexpr int U = WPL >= 4 ? 1 : 4 / WPL;
-        for (uint32_t e0 = b0; e0 < b1; e0 += U) {
-            uint32_t col[U];
-            bool ok[U];
+        for (uint32_t g0 = b0; g0 < b1; g0 += 32) {
+            const uint32_t e = g0 + lane;
+            const uint32_t mine = e < b1 ? (uint32_t)list[e] : 0u;
+            const bool pass = e < b1 && (!last || (mine >> G.ep[s]) == close_bits);
+            uint32_t pending = __ballot_sync(0xffffffffu, pass);
+            while (pending) {
+                uint32_t col[U];
+                bool ok[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                ok[u] = e0 + u < b1;
-                col[u] = ok[u] ? (uint32_t)list[e0 + u] : 0u;
-                if (last && ok[u] && (col[u] >> G.ep[s]) != close_bits) ok[u] = false;   // ring closure (Alg. 3 step 1)
-            }
-            uint32_t v[U][WPL], lp[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (ok[u]) {
-                    load_col<WPL>(cube + col_word0(G, cs, s, col[u]), G.W, lane, v[u]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < WPL; ++k) v[u][k] = 0u;
+                for (int u = 0; u < U; ++u) {
+                    ok[u] = pending != 0;
+                    const uint32_t l = ok[u] ? (uint32_t)__ffs(pending) - 1 : 0u;
+                    col[u] = __shfl_sync(0xffffffffu, mine, l);
+                    if (ok[u]) pending &= pending - 1;
                 }
-                lp[u] = lp_part | ((col[u] & ((1u << G.ep[s]) - 1u)) << G.ring_off[s]);   // step 2
-            }
-            if (last) {
-                for (uint32_t j = 0; j < G.n_va; ++j) {                                     // step 3
-                    uint32_t w[U][WPL];
+                uint32_t v[U][WPL], lp[U];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        if (ok[u]) {
-                            load_col<WPL>(cube + col_word0(G, cs, G.n_ra + j, va_col(G, j, lp[u])), G.W, lane, w[u]);
+                for (int u = 0; u < U; ++u) {
+                    if (ok[u]) {
+                        load_col<WPL>(cube + col_word0(G, cs, s, col[u]), G.W, lane, v[u]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < WPL; ++k) v[u][k] = 0u;
+                    }
+                    lp[u] = lp_part | ((col[u] & ((1u << G.ep[s]) - 1u)) << G.ring_off[s]);   // step 2
+                }
+                if (last) {
+                    for (uint32_t j = 0; j < G.n_va; ++j) {                                     // step 3
+                        uint32_t w[U][WPL];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (ok[u]) {
+                                load_col<WPL>(cube + col_word0(G, cs, G.n_ra + j, va_col(G, j, lp[u])), G.W, lane, w[u]);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < WPL; ++k) w[u][k] = 0u;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+#pragma unroll
+                            for (int k = 0; k < WPL; ++k) v[u][k] &= w[u][k];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (!ok[u]) continue;
+                    uint32_t ones = 0;
+                    if (lane_live) {
+#pragma unroll
+                        for (int k = 0; k < WPL; ++k) ones += __popc(v[u][k] & acc[k]);
+                    }
+                    ones = warp_sum(ones);
+                    const uint32_t zeros = G.g - ones;
+                    if ((int64_t)zeros > zm) continue;                                   // step 4
+                    if (lane == 0) {
+                        if (!last) {
+                            Tuple o = tu;
+                            o.hc[s] = (uint16_t)col[u];
+                            mybuf[nbuf] = *reinterpret_cast<const uint4 *>(&o);
                         } else {
-#pragma unroll
-                            for (int k = 0; k < WPL; ++k) w[u][k] = 0u;
+                            // Thm. 2 estimate; Z = 0 is reported with Z = 1 and flagged.
+                            const double g = (double)G.g;
+                            const double eps = P.eps[cs];
+                            const uint32_t zs = zeros ? zeros : 1u;
+                            const double den = __dsub_rn(g, __dmul_rn(g, eps));
+                            double est = __dmul_rn(-g, log(__ddiv_rn((double)zs, den)));
+                            if (est < 0.0) est = 0.0;
+                            // a cbaa_host record: {ip, z_union, est, flags}
+                            mybuf[nbuf] = make_uint4(unmangle(G, (lp[u] << G.r) | cs), zeros,
+                                                     __float_as_uint((float)est), zeros ? 0u : CBAA_FLAG_SATURATED);
                         }
                     }
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-#pragma unroll
-                        for (int k = 0; k < WPL; ++k) v[u][k] &= w[u][k];
+                    if (++nbuf == 32) flush();
                 }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (!ok[u]) continue;
-                uint32_t ones = 0;
-                if (lane_live) {
-#pragma unroll
-                    for (int k = 0; k < WPL; ++k) ones += __popc(v[u][k] & acc[k]);
-                }
-                ones = warp_sum(ones);
-                const uint32_t zeros = G.g - ones;
-                if ((int64_t)zeros > zm) continue;                                   // step 4
-                if (lane == 0) {
-                    if (!last) {
-                        Tuple o = tu;
-                        o.hc[s] = (uint16_t)col[u];
-                        mybuf[nbuf] = *reinterpret_cast<const uint4 *>(&o);
-                    } else {
-                        // Thm. 2 estimate; Z = 0 is reported with Z = 1 and flagged.
-                        const double g = (double)G.g;
-                        const double eps = P.eps[cs];
-                        const uint32_t zs = zeros ? zeros : 1u;
-                        const double den = __dsub_rn(g, __dmul_rn(g, eps));
-                        double est = __dmul_rn(-g, log(__ddiv_rn((double)zs, den)));
-                        if (est < 0.0) est = 0.0;
-                        // a cbaa_host record: {ip, z_union, est, flags}
-                        mybuf[nbuf] = make_uint4(unmangle(G, (lp[u] << G.r) | cs), zeros,
-                                                 __float_as_uint((float)est), zeros ? 0u : CBAA_FLAG_SATURATED);
-                    }
-                }
-                if (++nbuf == 32) flush();
             }
         }
     }
