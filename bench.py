@@ -36,6 +36,20 @@ from paper_1901_06207_b300 import traffic as T  # noqa: E402
 METRIC = "packets/sec (Gpps) cube update + end-of-window detect ms; fraction of HBM/L2-atomic peak"
 
 
+def update_kernels(partitioned: bool, tuning: dict, n: int) -> int:
+    """Kernels of one update call: direct 1; row tiles count, scan, scatter, apply, plus the
+    overflow pass when run capacities come from a sample (tile_kind 3, or 0 for >= 8Mi packets)."""
+    if not partitioned:
+        return 1
+    k = tuning.get("tile_kind", 0)
+    return 5 if k == 3 or (k == 0 and n >= (8 << 20)) else 4
+
+
+def detect_kernels(geo: dict) -> int:
+    """Kernels of one detect: zero counts (with eps and Zmax), hot lists, |RA|-1 joins, sort."""
+    return 3 + (geo["n_ra"] - 1)
+
+
 def workload(name: str):
     from paper_1901_06207_b300.cbaa import make_params
     if name == "window64m":
@@ -279,7 +293,7 @@ def run_cbaa(args):
     info = torch.zeros(8, dtype=torch.int32, device=dev)
     # update (direct: 1 kernel; binned: count, scan, scatter, apply) | detect: zero counts, eps/zmax,
     # hot lists, |RA|-1 joins, rank sort, sort/status
-    kernels_per_step = (4 if uws is not None else 1) + 3 + (geo["n_ra"] - 1) + 2
+    kernels_per_step = update_kernels(uws is not None, C.get_tuning(), n) + detect_kernels(geo)
 
     def do_update(c=None, src=None):
         c = cube if c is None else c
@@ -574,7 +588,9 @@ def run_sharded(args):
                                "sketches, restore them, all-gather of the host lists (host-synchronous, "
                                "timed on the host clock)",
                        "parallelism": f"{world} ranks, sketches split {1 << geo['r']} / {world}"},
-            "hosts_detected": int(hosts.size), "gpu_launches": steps * (4 + 7 + (1 if world > 1 else 0)),
+            "hosts_detected": int(hosts.size),
+            "gpu_launches": steps * (update_kernels(True, C.get_tuning(), n) + detect_kernels(geo) +
+                                     (1 if world > 1 else 0)),
             "clocks": clocks.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -680,7 +696,8 @@ def run_batched(args):
             "plain_single_cube": {"value": plain_value, "unit": "Gpps", "window_ms": plain_ms / steps / len(wins),
                                   "path": "one cube, partitioned update of the whole window, detect, no graph"},
             "hosts_per_window": [int(i["n_hosts"]) for _, i in res],
-            "gpu_launches": steps * len(wins) * (4 + 1 + 3 + (geo["n_ra"] - 1) + 2),
+            "gpu_launches": steps * len(wins) * (update_kernels(True, C.get_tuning(), sum(n_per) // len(wins)) + 1 +
+                                                 detect_kernels(geo)),
             "clocks": clocks.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

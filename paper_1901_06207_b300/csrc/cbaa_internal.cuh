@@ -136,5 +136,5 @@ cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint
 // Zero counts, ε and Zmax of the sketches [cs_lo, cs_hi) (cs_hi = 0: all).
 cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc, uint64_t *za,
                                 double *eps, int64_t *zmax, double E, cudaStream_t s, uint32_t cs_lo = 0,
-                                uint32_t cs_hi = 0);
+                                uint32_t cs_hi = 0, uint32_t *done = nullptr);
 }  // namespace cbaa

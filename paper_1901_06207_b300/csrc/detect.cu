@@ -290,21 +290,67 @@ __global__ void __launch_bounds__(256) k_join(const Geo G, const uint32_t *__res
     if (nbuf) flush();
 }
 
-// Host lists of up to kRankMax entries are sorted by rank: every thread owns
-// one host and counts the hosts with a smaller ip (ties broken by index),
-// which is its place in the output; the keys are read tile by tile through
-// shared memory.  Longer lists go through the bitonic network in
-// k_sort_out.
+// Sorting the host list by ip, writing the first min(n, cap) to `out`, and
+// settling the status, in one launch.  Lists of up to kRankMax entries are
+// sorted by rank: every thread owns one host and counts the hosts with a
+// smaller ip (ties broken by index), which is its place in the output; the
+// keys are read tile by tile through shared memory.  Longer lists go through
+// a bitonic network over (ip << 32 | index) keys in block 0 (in shared memory
+// up to kSmemKeys keys, else in the workspace).  The status depends only on
+// the stage counts, which are final when this kernel runs; block 0 writes it.
 constexpr uint32_t kRankMax = 1u << 16;
 constexpr uint32_t kRankThreads = 256;
 constexpr uint32_t kRankLanes = 8;               // lanes sharing one host's count
 constexpr uint32_t kRankTile = 4096;
+constexpr uint32_t kSmemKeys = 4096;
 
-__global__ void __launch_bounds__(kRankThreads) k_rank_sort(WsPtrs P, cbaa_host *__restrict__ out, uint64_t cap) {
+__device__ void bitonic_out(WsPtrs P, uint32_t n, cbaa_host *__restrict__ out, uint64_t cap,
+                            unsigned long long *skeys) {
+    uint32_t N = 1;
+    while (N < n) N <<= 1;
+    unsigned long long *keys = (N <= kSmemKeys) ? skeys : P.keys;
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
+        keys[k] = (k < n) ? (((unsigned long long)P.hosts[k].ip << 32) | k) : ~0ull;
+    __syncthreads();
+    for (uint32_t size = 2; size <= N; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t t = threadIdx.x; t < N / 2; t += blockDim.x) {
+                const uint32_t lo = 2 * t - (t & (stride - 1));
+                const uint32_t hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = keys[lo], b = keys[hi];
+                if ((a > b) == up) { keys[lo] = b; keys[hi] = a; }
+            }
+            __syncthreads();
+        }
+    }
+    const uint64_t nw = n < cap ? n : cap;
+    for (uint32_t k = threadIdx.x; k < nw; k += blockDim.x) out[k] = P.hosts[keys[k] & 0xFFFFFFFFull];
+}
+
+__global__ void __launch_bounds__(kRankThreads) k_sort(const Geo G, WsPtrs P, cbaa_host *__restrict__ out,
+                                                       uint64_t cap) {
     __shared__ uint32_t keys[kRankTile];
-    const uint32_t found = P.state->info.n_hosts;
+    __shared__ unsigned long long skeys[kSmemKeys];
+    DevState *st = P.state;
+    const uint32_t found = st->info.n_hosts;
     const uint32_t n = found < P.m ? found : P.m;
-    if (n > kRankMax) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t need = 0, tuples = 0;
+        for (uint32_t s = 0; s + 1 < G.n_ra; ++s) {
+            const uint32_t c = st->stage_count[s];
+            tuples += c;
+            if (c > P.m && c > need) need = c;
+        }
+        if (found > P.m && found > need) need = found;
+        st->info.n_tuples = tuples;
+        st->info.need_tuples = need;
+        st->info.status = need ? CBAA_ERR_WORKSPACE : (found > cap ? CBAA_ERR_CAPACITY : CBAA_OK);
+    }
+    if (n > kRankMax) {
+        if (blockIdx.x == 0) bitonic_out(P, n, out, cap, skeys);
+        return;
+    }
     constexpr uint32_t per_block = kRankThreads / kRankLanes;
     if ((uint64_t)blockIdx.x * per_block >= n) return;
     const uint32_t sub = threadIdx.x % kRankLanes;
@@ -333,54 +379,6 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_sort(WsPtrs P, cbaa_host 
     if (sub == 0 && i < n && rank < cap) out[rank] = P.hosts[i];
 }
 
-// Sort the restored hosts by ip (bitonic network over (ip << 32 | index)
-// keys, in shared memory up to kSmemKeys keys, else in the workspace) when
-// the list is longer than k_rank_sort takes, write the first min(n, cap) to
-// `out`, and settle the status.
-constexpr uint32_t kSmemKeys = 4096;
-
-__global__ void __launch_bounds__(1024) k_sort_out(const Geo G, WsPtrs P, cbaa_host *__restrict__ out, uint64_t cap) {
-    __shared__ unsigned long long skeys[kSmemKeys];
-    DevState *st = P.state;
-    const uint32_t found = st->info.n_hosts;
-    const uint32_t n = found < P.m ? found : P.m;
-    uint32_t N = 1;
-    while (N < n) N <<= 1;
-    if (n <= kRankMax) N = 0;                     // sorted by k_rank_sort
-    unsigned long long *keys = (N <= kSmemKeys) ? skeys : P.keys;
-    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
-        keys[k] = (k < n) ? (((unsigned long long)P.hosts[k].ip << 32) | k) : ~0ull;
-    __syncthreads();
-    for (uint32_t size = 2; size <= N; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t t = threadIdx.x; t < N / 2; t += blockDim.x) {
-                const uint32_t lo = 2 * t - (t & (stride - 1));
-                const uint32_t hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const unsigned long long a = keys[lo], b = keys[hi];
-                if ((a > b) == up) { keys[lo] = b; keys[hi] = a; }
-            }
-            __syncthreads();
-        }
-    }
-    const uint64_t nw = n < cap ? n : cap;
-    if (N)
-        for (uint32_t k = threadIdx.x; k < nw; k += blockDim.x)
-            out[k] = P.hosts[keys[k] & 0xFFFFFFFFull];
-    if (threadIdx.x == 0) {
-        uint32_t need = 0, tuples = 0;
-        for (uint32_t s = 0; s + 1 < G.n_ra; ++s) {
-            const uint32_t c = st->stage_count[s];
-            tuples += c;
-            if (c > P.m && c > need) need = c;
-        }
-        if (found > P.m && found > need) need = found;
-        st->info.n_tuples = tuples;
-        st->info.need_tuples = need;
-        st->info.status = need ? CBAA_ERR_WORKSPACE : (found > cap ? CBAA_ERR_CAPACITY : CBAA_OK);
-    }
-}
-
 template <int WPL>
 cudaError_t launch_join(const Geo &G, const uint32_t *cube, const WsPtrs &P, uint32_t s, unsigned blocks, cudaStream_t st) {
     k_join<WPL><<<blocks, 256, 0, st>>>(G, cube, P, s);
@@ -401,7 +399,7 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
 
     cudaError_t e = cudaMemsetAsync(P.state, 0, sizeof(DevState), s);
     if (e != cudaSuccess) return CBAA_ERR_CUDA;
-    e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s, cs_lo, cs_hi);
+    e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s, cs_lo, cs_hi, &P.state->stats_done);
     if (e != cudaSuccess) return CBAA_ERR_CUDA;
     k_hot_lists<<<dim3(cs_hi - cs_lo, G.n_ra), 1024, 0, s>>>(G, P, cs_lo);
     if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
@@ -422,9 +420,8 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
     const uint64_t dcap = out ? cap : P.m;
     const uint64_t rank_n = P.m < kRankMax ? P.m : kRankMax;
     const uint64_t per_block = kRankThreads / kRankLanes;
-    k_rank_sort<<<(unsigned)((rank_n + per_block - 1) / per_block), kRankThreads, 0, s>>>(P, dst, dcap);
-    if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
-    k_sort_out<<<1, 1024, 0, s>>>(G, P, dst, dcap);
+    const uint64_t sort_blocks = (rank_n + per_block - 1) / per_block;
+    k_sort<<<(unsigned)(sort_blocks ? sort_blocks : 1), kRankThreads, 0, s>>>(G, P, dst, dcap);
     if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
     if (info_copy) {
         e = cudaMemcpyAsync(info_copy, &P.state->info, sizeof(cbaa_detect_info), cudaMemcpyDeviceToDevice, s);

@@ -18,7 +18,8 @@ static_assert(sizeof(Tuple) == 16, "tuple is one 16-byte record");
 struct DevState {
     cbaa_detect_info info;
     uint32_t stage_count[CBAA_MAX_RA];   // [0] = seed tuples (hot columns of RA 0), [s] = output of join stage s
-    uint32_t pad[2];
+    uint32_t stats_done;                 // zero-count blocks finished (the last computes eps and Zmax)
+    uint32_t pad;
 };
 
 struct WsLayout {

@@ -109,6 +109,32 @@ __global__ void __launch_bounds__(256) k_merge(uint4 *__restrict__ dst, const Sr
 }
 
 // ---------------------------------------------------------------------------
+// Thm. 1 with measured one-bit fractions, then the hot-column bound, for one
+// sketch.  Each operation is a correctly rounded IEEE double operation in a
+// fixed order (explicit _rn intrinsics, so nothing is contracted into an
+// FMA).  za is read from L2 (__ldcg): other blocks' atomics put it there.
+__device__ void eps_zmax_of(const Geo &G, const unsigned long long *za, double E, uint32_t cs,
+                            double *__restrict__ eps_out, int64_t *__restrict__ zmax_out) {
+    double eps = 1.0;
+    for (uint32_t a = 0; a < G.A; ++a) {
+        const unsigned long long bits = (unsigned long long)(1u << G.cbn[a]) << G.log2_g;
+        const unsigned long long ones = bits - __ldcg(za + (size_t)cs * G.A + a);
+        const double p1 = __ddiv_rn(__ull2double_rn(ones), __ull2double_rn(bits));
+        eps = __dmul_rn(eps, p1);
+    }
+    const double g = (double)G.g;
+    double t;
+    if (G.form == 1) {
+        const double b = __dmul_rn(__dmul_rn(g, __dadd_rn(1.0, eps)), E);
+        t = __dsub_rn(b, __dmul_rn(g, eps));
+    } else {
+        t = __dmul_rn(__dmul_rn(g, __dsub_rn(1.0, eps)), E);
+    }
+    if (eps_out) eps_out[cs] = eps;
+    if (zmax_out) zmax_out[cs] = (int64_t)floor(t);
+}
+
+// ---------------------------------------------------------------------------
 // Zero counts.  Block (cs*A + a, split) walks a slice of array a of sketch
 // cs.  TPC threads share one column, each summing the popcounts of its
 // PER 16-byte pieces (TPC = W/(4 ZC_PIECES) clamped to [1, 32], so a
@@ -122,10 +148,15 @@ __global__ void __launch_bounds__(256) k_merge(uint4 *__restrict__ dst, const Sr
 #define ZC_U 2
 #endif
 
+// With `done` set, the last block to finish also computes eps and Zmax of the
+// sketches [cs_lo, cs_hi) (one launch fewer in the detect); done counts the
+// finished blocks and must start at zero.
 __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t *__restrict__ cube,
                                                      uint16_t *__restrict__ zc,
                                                      unsigned long long *__restrict__ za, uint32_t splits,
-                                                     uint32_t arr0) {
+                                                     uint32_t arr0, uint32_t *__restrict__ done, double E,
+                                                     double *__restrict__ eps_out, int64_t *__restrict__ zmax_out,
+                                                     uint32_t cs_lo, uint32_t cs_hi) {
     const uint32_t arr = arr0 + blockIdx.x;          // cs*A + a
     const uint32_t cs = arr / G.A, a = arr % G.A;
     const uint32_t ncol = 1u << G.cbn[a];
@@ -172,38 +203,30 @@ __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t
     __shared__ unsigned long long part[8];
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
     __syncthreads();
+    __shared__ bool s_last;
     if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += part[w];
         atomicAdd(&za[arr], t);
+        s_last = false;
+        if (done) {
+            __threadfence();
+            s_last = atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1;
+        }
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (uint32_t cs = cs_lo + threadIdx.x; cs < cs_hi; cs += blockDim.x) eps_zmax_of(G, za, E, cs, eps_out, zmax_out);
     }
 }
 
-// Thm. 1 with measured one-bit fractions, then the hot-column bound.  Each
-// operation is a correctly rounded IEEE double operation in a fixed order
-// (explicit _rn intrinsics, so nothing is contracted into an FMA).
+// eps and Zmax of the sketches [cs_lo, cs_hi) (eps_zmax_of).
 __global__ void k_eps_zmax(const Geo G, const unsigned long long *__restrict__ za, double E,
                            double *__restrict__ eps_out, int64_t *__restrict__ zmax_out, uint32_t cs_lo,
                            uint32_t cs_hi) {
     const uint32_t cs = cs_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (cs >= cs_hi) return;
-    double eps = 1.0;
-    for (uint32_t a = 0; a < G.A; ++a) {
-        const unsigned long long bits = (unsigned long long)(1u << G.cbn[a]) << G.log2_g;
-        const unsigned long long ones = bits - za[(size_t)cs * G.A + a];
-        const double p1 = __ddiv_rn(__ull2double_rn(ones), __ull2double_rn(bits));
-        eps = __dmul_rn(eps, p1);
-    }
-    const double g = (double)G.g;
-    double t;
-    if (G.form == 1) {
-        const double b = __dmul_rn(__dmul_rn(g, __dadd_rn(1.0, eps)), E);
-        t = __dsub_rn(b, __dmul_rn(g, eps));
-    } else {
-        t = __dmul_rn(__dmul_rn(g, __dsub_rn(1.0, eps)), E);
-    }
-    if (eps_out) eps_out[cs] = eps;
-    if (zmax_out) zmax_out[cs] = (int64_t)floor(t);
+    if (cs < cs_hi) eps_zmax_of(G, za, E, cs, eps_out, zmax_out);
 }
 
 }  // namespace
@@ -255,7 +278,7 @@ cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint
 
 cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc, uint64_t *za,
                                 double *eps, int64_t *zmax, double E, cudaStream_t s, uint32_t cs_lo,
-                                uint32_t cs_hi) {
+                                uint32_t cs_hi, uint32_t *done) {
     if (cs_hi == 0) cs_hi = G.smask + 1;
     cudaError_t e = cudaMemsetAsync(za, 0, sizeof(uint64_t) * (size_t)(G.smask + 1) * G.A, s);
     if (e != cudaSuccess) return e;
@@ -266,11 +289,13 @@ cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc
     while ((uint64_t)arrays * splits < (uint64_t)num_sms() * 8 && splits < 64) splits <<= 1;
     const uint32_t min_cols = 1u << 5;   // cbn >= 5 for every array
     if (splits > min_cols) splits = min_cols;
+    const bool fused = done && (eps || zmax);
     k_zero_counts<<<dim3(arrays, splits), 256, 0, s>>>(G, cube, zc, reinterpret_cast<unsigned long long *>(za), splits,
-                                                       cs_lo * G.A);
+                                                       cs_lo * G.A, fused ? done : nullptr, E, eps, zmax, cs_lo,
+                                                       cs_hi);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (eps || zmax) {
+    if ((eps || zmax) && !fused) {
         const uint32_t S = cs_hi - cs_lo;
         k_eps_zmax<<<(S + 127) / 128, 128, 0, s>>>(G, reinterpret_cast<const unsigned long long *>(za), E, eps, zmax,
                                                    cs_lo, cs_hi);
