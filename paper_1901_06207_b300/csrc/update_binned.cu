@@ -126,42 +126,6 @@ __device__ __forceinline__ uint32_t source_tiles(const Geo &G, uint32_t seg_base
     return nra + nva;
 }
 
-// Exclusive scan of in[0..n) into out[0..n) by one block (blockDim a
-// multiple of 32, at most 1024); returns the total.  `tmp` holds 32 words.
-__device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *tmp) {
-    const uint32_t T = blockDim.x, t = threadIdx.x, lane = t & 31u, warp = t >> 5;
-    const uint32_t per = (n + T - 1) / T;
-    const uint32_t b0 = t * per < n ? t * per : n;
-    const uint32_t b1 = b0 + per < n ? b0 + per : n;
-    uint32_t s = 0;
-    for (uint32_t i = b0; i < b1; ++i) s += in[i];
-    uint32_t x = s;                                   // inclusive warp scan of thread sums
-    for (uint32_t o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) tmp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t v = lane < T / 32 ? tmp[lane] : 0u;
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        tmp[lane] = v;                                // inclusive over warps
-    }
-    __syncthreads();
-    uint32_t run = (warp ? tmp[warp - 1] : 0u) + x - s;
-    const uint32_t total = tmp[T / 32 - 1];
-    for (uint32_t i = b0; i < b1; ++i) {
-        const uint32_t v = in[i];
-        out[i] = run;
-        run += v;
-    }
-    __syncthreads();
-    return total;
-}
-
 template <int NRA, int NVA>
 __global__ void __launch_bounds__(kCountThreads) k_bin_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                              uint32_t *__restrict__ counts) {
@@ -205,31 +169,13 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(const Geo G, const 
         if (hist[i]) atomicAdd(&counts[i], hist[i]);
 }
 
-// One block: offsets = exclusive scan of counts, cursors = offsets,
-// items = exclusive scan of ceil(counts / ch) (item_start[nb] = total).
-// samp > 1: counts are those of a 1-in-samp sample of the packets and are
-// first replaced by run capacities (sample_capacity).
+// One block: bin_scan_block.
 __global__ void __launch_bounds__(1024) k_bin_scan(uint32_t *__restrict__ counts, uint32_t nb, uint32_t ch,
                                                    uint32_t *__restrict__ offsets, uint32_t *__restrict__ cursors,
                                                    uint32_t *__restrict__ item_start, uint32_t *__restrict__ nchunk,
                                                    uint32_t samp) {
     __shared__ uint32_t tmp[32];
-    if (samp > 1) {
-        for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) counts[i] = sample_capacity(counts[i], samp);
-        __syncthreads();
-    }
-    const uint32_t total = block_exclusive_scan(counts, offsets, nb, tmp);
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
-        cursors[i] = offsets[i];
-        nchunk[i] = (counts[i] + ch - 1) / ch;
-    }
-    if (threadIdx.x == 0) offsets[nb] = total;
-    __syncthreads();
-    const uint32_t items = block_exclusive_scan(nchunk, item_start, nb, tmp);
-    if (threadIdx.x == 0) {
-        item_start[nb] = items;
-        nchunk[nb] = 0;                // queue counter of the row-tile apply
-    }
+    bin_scan_block(counts, nb, ch, offsets, cursors, item_start, nchunk, samp, tmp);
 }
 
 // THREADS x PPT packets per block.

@@ -38,7 +38,9 @@ struct BinWs {
 
 inline size_t bin_align(size_t x) { return (x + 255) / 256 * 256; }
 
-inline size_t bin_ws_fixed(uint32_t nb) { return 5 * bin_align(sizeof(uint32_t) * ((size_t)nb + 1)); }
+// Five tables of nb + 2 words: per-tile counts (counts[nb] and counts[nb + 1]
+// are counters of the row-tile path), offsets, cursors, item starts, chunks.
+inline size_t bin_ws_fixed(uint32_t nb) { return 5 * bin_align(sizeof(uint32_t) * ((size_t)nb + 2)); }
 
 // Row tiles (update_rowtile.cu): one per (cube, sketch, row word), each
 // holding one word of every column of its sketch.
@@ -69,7 +71,7 @@ inline bool bin_ws_make(const Geo &G, uint32_t n_cubes, void *base, size_t bytes
     const size_t cap = (size_t)(1u << 31) / G.A;            // code offsets stay 32-bit
     if (m > cap) m = cap;
     char *b = static_cast<char *>(base);
-    const size_t step = bin_align(sizeof(uint32_t) * ((size_t)nb + 1));
+    const size_t step = bin_align(sizeof(uint32_t) * ((size_t)nb + 2));
     W->counts = reinterpret_cast<uint32_t *>(b);
     W->offsets = reinterpret_cast<uint32_t *>(b + step);
     W->cursors = reinterpret_cast<uint32_t *>(b + 2 * step);
@@ -101,6 +103,72 @@ __host__ __device__ inline uint32_t sample_capacity(uint32_t c, uint32_t samp) {
     const uint64_t cap = est + est / 8 + 4ull * samp * r + 256;
     return cap > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap;
 }
+
+#ifdef __CUDACC__
+// Exclusive scan of in[0..n) into out[0..n) by one block (blockDim a
+// multiple of 32, at most 1024; in == out allowed); returns the total.
+// `tmp` is 32 words of shared memory.
+__device__ inline uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *tmp) {
+    const uint32_t T = blockDim.x, t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+    const uint32_t per = (n + T - 1) / T;
+    const uint32_t b0 = t * per < n ? t * per : n;
+    const uint32_t b1 = b0 + per < n ? b0 + per : n;
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i) s += in[i];
+    uint32_t x = s;                                   // inclusive warp scan of thread sums
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < T / 32 ? tmp[lane] : 0u;
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        tmp[lane] = v;                                // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t run = (warp ? tmp[warp - 1] : 0u) + x - s;
+    const uint32_t total = tmp[T / 32 - 1];
+    for (uint32_t i = b0; i < b1; ++i) {
+        const uint32_t v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    __syncthreads();
+    return total;
+}
+
+// By one block: offsets = exclusive scan of counts (offsets[nb] = total),
+// cursors = offsets, items = exclusive scan of ceil(counts / ch)
+// (item_start[nb] = total), and the assembly's queue counters nchunk[nb] and
+// nchunk[nb + 1] = 0.
+// samp > 1: counts are those of a 1-in-samp sample of the packets and are
+// first replaced by run capacities (sample_capacity).
+__device__ inline void bin_scan_block(uint32_t *counts, uint32_t nb, uint32_t ch, uint32_t *offsets, uint32_t *cursors,
+                                      uint32_t *item_start, uint32_t *nchunk, uint32_t samp, uint32_t *tmp) {
+    if (samp > 1) {
+        for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) counts[i] = sample_capacity(counts[i], samp);
+        __syncthreads();
+    }
+    const uint32_t total = block_exclusive_scan(counts, offsets, nb, tmp);
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+        cursors[i] = offsets[i];
+        nchunk[i] = (counts[i] + ch - 1) / ch;
+    }
+    if (threadIdx.x == 0) offsets[nb] = total;
+    __syncthreads();
+    const uint32_t items = block_exclusive_scan(nchunk, item_start, nb, tmp);
+    if (threadIdx.x == 0) {
+        item_start[nb] = items;
+        nchunk[nb] = 0;
+        nchunk[nb + 1] = 0;
+    }
+}
+#endif
 
 // Upper bound of sum_b sample_capacity(c_b, samp) when m packets are
 // sampled in tiles of `tile` (sum_b c_b <= m/samp + tile): the estimates sum

@@ -6,19 +6,23 @@
 // at most 128 KiB.  All |RA|+|VA| bits of a packet fall into the same row
 // tile (they share the sketch and the row, Alg. 1), so a packet is routed
 // once, as a record {LP, bit position} (4 bytes when r >= 5, else the
-// 8 bytes {mangled iip, row}); the tile
-// assembly recomputes its columns (the ring reads and the VA hash of
-// Alg. 1) and sets its bits with shared-memory atomics, then ORs every
-// non-zero word into the cube (the words of a row tile are one per column,
-// W words apart in the cube).
+// 8 bytes {mangled iip, row}); the tile assembly recomputes its columns (the
+// ring reads and the VA hash of Alg. 1) and sets its bits with shared-memory
+// atomics, then ORs every non-zero word into the cube (the words of a row
+// tile are one per column, W words apart in the cube).
 //
-//   1. k_rt_count   : packets per row tile (one shared-memory atomic per packet)
-//   2. k_bin_scan   : (shared with the column-tile path) offsets and apply items
-//   3. k_rt_scatter : a block stages its packets' records grouped by row tile
-//                     and writes each run out coalesced
-//   4. k_rt_apply   : per item, assemble the row tile in shared memory, flush
-// Traffic per packet: 8 B read twice, a 4-byte (r >= 5) or 8-byte record
-// written and read once.
+//   1. k_rt_count   : packets per row tile (one shared-memory atomic per
+//                     packet), of every packet or of a 1-in-16 sample
+//      k_bin_scan   : (shared with the column-tile path) the runs' offsets
+//                     (or sampled capacities) and the assembly items
+//   2. k_rt_scatter : a block stages its packets' records grouped by row tile
+//                     and writes each run out coalesced; with sampled
+//                     capacities, records past a run's capacity go to an
+//                     overflow list
+//   3. k_rt_apply   : per item, assemble the row tile in shared memory and
+//                     flush it; then the overflow list, by direct reductions
+// Traffic per packet: 8 B read once (plus 8 B more when every packet is
+// counted), a 4-byte (r >= 5) or 8-byte record written and read once.
 #include <mutex>
 
 #include "cbaa_internal.cuh"
@@ -84,39 +88,6 @@ __device__ __forceinline__ uint32_t tile_off(const Geo &G, uint32_t a, uint32_t 
     return G.col_base[a] + col;
 }
 
-__device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *tmp) {
-    const uint32_t T = blockDim.x, t = threadIdx.x, lane = t & 31u, warp = t >> 5;
-    const uint32_t per = (n + T - 1) / T;
-    const uint32_t b0 = t * per < n ? t * per : n;
-    const uint32_t b1 = b0 + per < n ? b0 + per : n;
-    uint32_t s = 0;
-    for (uint32_t i = b0; i < b1; ++i) s += in[i];
-    uint32_t x = s;
-    for (uint32_t o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) tmp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t v = lane < T / 32 ? tmp[lane] : 0u;
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        tmp[lane] = v;
-    }
-    __syncthreads();
-    uint32_t run = (warp ? tmp[warp - 1] : 0u) + x - s;
-    const uint32_t total = tmp[T / 32 - 1];
-    for (uint32_t i = b0; i < b1; ++i) {
-        const uint32_t v = in[i];
-        out[i] = run;
-        run += v;
-    }
-    __syncthreads();
-    return total;
-}
 
 __device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
     uint4 v;
@@ -134,9 +105,9 @@ __device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
 constexpr uint32_t kCountTile = 4 * kCountThreads;
 
 // ORIENT (the cube has an inner network): packets are raw {src, dst} (orient()).
-template <bool MULTI, bool ORIENT>
 // samp > 1: only every samp-th tile of kCountTile packets is counted (a
 // sample for run capacities, see sample_capacity).
+template <bool MULTI, bool ORIENT>
 __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                             uint32_t *__restrict__ counts, uint32_t samp) {
     extern __shared__ uint32_t hist[];
@@ -145,8 +116,8 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
         const uint64_t tiles = (n + kCountTile - 1) / kCountTile;
         const uint64_t per = ((tiles + gridDim.x - 1) / gridDim.x + samp - 1) / samp * samp;
         lo = (uint64_t)blockIdx.x * per * kCountTile;
-        if (lo >= n) return;                               // the whole block leaves before any barrier
         hi = lo + per * kCountTile < n ? lo + per * kCountTile : n;
+        if (lo > hi) lo = hi;                              // a block past the end counts nothing
         step = (uint64_t)kCountTile * samp;
     } else {
         lo = (uint64_t)blockIdx.x * kCountTile * samp;
@@ -154,10 +125,10 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
         step = (uint64_t)gridDim.x * kCountTile * samp;
     }
     BlockTiles B;
-    if (MULTI) {
+    if (MULTI && lo < hi) {
         B = block_tiles(G, S, lo, hi - 1, nb);
     } else {
-        B.s_lo = 0; B.nbl = nb; B.tpr = (G.smask + 1) * G.W; B.local = false;
+        B.s_lo = 0; B.nbl = MULTI ? 0u : nb; B.tpr = (G.smask + 1) * G.W; B.local = false;
     }
     for (uint32_t i = threadIdx.x; i < B.nbl; i += blockDim.x) hist[i] = 0;
     __syncthreads();
@@ -349,6 +320,36 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     }
 }
 
+// One overflow entry of a sampled pass: a record that did not fit its run's
+// capacity sets its |RA|+|VA| bits straight in the cube (one L2 reduction per
+// bit, as the direct update does).  Entries are {record, tile} for 4-byte
+// records, {mangled ip, row | cube << 16} otherwise.
+template <bool SHORT>
+__device__ __forceinline__ void overflow_entry(const Geo &G, const BinSegs &S, uint2 e) {
+    const uint32_t tpr = (G.smask + 1) * G.W;
+    uint32_t lp, bit, router, cs, w;
+    if (SHORT) {
+        lp = e.x >> 5;
+        bit = e.x & 31u;
+        router = e.y / tpr;
+        const uint32_t rem = e.y - router * tpr;
+        cs = rem / G.W;
+        w = rem - cs * G.W;
+    } else {
+        const uint32_t row = e.y & 0xFFFFu;
+        router = e.y >> 16;
+        cs = e.x & G.smask;
+        lp = e.x >> G.r;
+        w = row >> 5;
+        bit = row & 31u;
+    }
+    uint32_t *base = S.cube[router] + (size_t)cs * G.cs_words + w;
+    for (uint32_t a = 0; a < G.A; ++a) {
+        const uint32_t col = a < G.n_ra ? ra_col(G, a, lp) : va_col(G, a - G.n_ra, lp);
+        red_or(base + G.arr_base[a] + (size_t)col * G.W, 1u << bit);
+    }
+}
+
 // Items (a row tile's records, cut into chunks of ch only when a tile holds
 // more than ch) are taken from a queue, so blocks that drew small tiles take
 // more of them.
@@ -385,7 +386,9 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
                                                             const uint32_t *__restrict__ item_start, uint32_t nb,
                                                             uint32_t ch, uint32_t tile_words,
                                                             uint32_t *__restrict__ queue,
-                                                            const uint32_t *__restrict__ cursors) {
+                                                            const uint32_t *__restrict__ cursors,
+                                                            const uint2 *__restrict__ ovf,
+                                                            const uint32_t *__restrict__ ovf_count, uint32_t ovf_cap) {
     extern __shared__ uint32_t tile[];
     __shared__ uint32_t s_item;
     const uint32_t items = item_start[nb];
@@ -435,40 +438,18 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
         }
         __syncthreads();
     }
-}
-
-// Records of a sampled pass that did not fit their run's capacity: each sets
-// its |RA|+|VA| bits straight in the cube (one L2 reduction per bit, as the
-// direct update does).  The count is read on the device, so a pass without
-// overflow costs one short launch.
-template <bool SHORT>
-__global__ void __launch_bounds__(256) k_rt_overflow(const Geo G, const BinSegs S, const uint2 *__restrict__ ovf,
-                                                     const uint32_t *__restrict__ ovf_count, uint32_t cap) {
-    const uint32_t n = *ovf_count < cap ? *ovf_count : cap;
-    const uint32_t tpr = (G.smask + 1) * G.W;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint2 e = ovf[i];
-        uint32_t lp, bit, router, cs, w;
-        if (SHORT) {
-            lp = e.x >> 5;
-            bit = e.x & 31u;
-            router = e.y / tpr;
-            const uint32_t rem = e.y - router * tpr;
-            cs = rem / G.W;
-            w = rem - cs * G.W;
-        } else {
-            const uint32_t row = e.y & 0xFFFFu;
-            router = e.y >> 16;
-            cs = e.x & G.smask;
-            lp = e.x >> G.r;
-            w = row >> 5;
-            bit = row & 31u;
-        }
-        uint32_t *base = S.cube[router] + (size_t)cs * G.cs_words + w;
-        for (uint32_t a = 0; a < G.A; ++a) {
-            const uint32_t col = a < G.n_ra ? ra_col(G, a, lp) : va_col(G, a - G.n_ra, lp);
-            red_or(base + G.arr_base[a] + (size_t)col * G.W, 1u << bit);
-        }
+    // a sampled pass: blocks leaving the item queue take chunks of the overflow list
+    if (!ovf) return;
+    const uint32_t n_ovf = *ovf_count < ovf_cap ? *ovf_count : ovf_cap;
+    constexpr bool SHORT = sizeof(Rec) == 4;
+    for (;;) {
+        __syncthreads();                                  // every thread has read the previous chunk
+        if (threadIdx.x == 0) s_item = atomicAdd(queue + 1, 1u);
+        __syncthreads();
+        const uint64_t c0 = (uint64_t)s_item * blockDim.x;
+        if (c0 >= n_ovf) break;
+        const uint64_t c = c0 + threadIdx.x;
+        if (c < n_ovf) overflow_entry<SHORT>(G, S, ovf[c]);
     }
 }
 
@@ -548,7 +529,8 @@ cudaError_t launch_rt_scatter_kind(const Geo &G, const BinSegs &S, uint64_t m, u
 
 template <typename Rec>
 cudaError_t launch_rt_apply(const Geo &G, const BinSegs &S, const BinWs &W, uint32_t nb, uint32_t ch, uint32_t tw,
-                            size_t smem, int sms, cudaStream_t s) {
+                            size_t smem, int sms, const uint2 *ovf, const uint32_t *ovf_count, uint32_t ovf_cap,
+                            cudaStream_t s) {
     const bool three_one = G.n_ra == 3 && G.n_va == 1;
     auto kapply = three_one ? k_rt_apply<3, 1, Rec> : k_rt_apply<0, 0, Rec>;
     cudaError_t e = allow_smem(kapply, smem);
@@ -559,7 +541,7 @@ cudaError_t launch_rt_apply(const Geo &G, const BinSegs &S, const BinWs &W, uint
         per_sm = 1;
     kapply<<<(unsigned)(sms * per_sm), kApplyThreads, smem, s>>>(G, S, reinterpret_cast<const Rec *>(W.codes),
                                                                  W.offsets, W.item_start, nb, ch, tw, W.nchunk + nb,
-                                                                 W.cursors);
+                                                                 W.cursors, ovf, ovf_count, ovf_cap);
     return cudaGetLastError();
 }
 
@@ -637,11 +619,11 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
         const uint64_t want = (m + (uint64_t)kCountTile * samp - 1) / ((uint64_t)kCountTile * samp);
         const uint64_t cap = (uint64_t)sms * count_bps;
         const unsigned cgrid = (unsigned)(want < cap ? want : cap);
-        kcount<<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts, samp);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // split a row tile only when it holds more than apply_ips/2 times the average tile
         uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
         if (ch < (1u << 12)) ch = 1u << 12;
+        kcount<<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts, samp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s, samp)) != cudaSuccess) return e;
         Overflow O{nullptr, nullptr, 0};
         if (sampled) {
@@ -655,14 +637,11 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
             e = ori ? launch_rt_scatter_kind<false, true>(G, S, m, nb, W, O, T.scatter_shape, s)
                     : launch_rt_scatter_kind<false, false>(G, S, m, nb, W, O, T.scatter_shape, s);
         if (e != cudaSuccess) return e;
-        e = short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s)
-                      : launch_rt_apply<uint2>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, s);
+        e = short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, O.list, O.count,
+                                                  O.cap, s)
+                      : launch_rt_apply<uint2>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, O.list, O.count, O.cap,
+                                               s);
         if (e != cudaSuccess) return e;
-        if (sampled) {
-            if (short_rec) k_rt_overflow<true><<<(unsigned)sms * 2, 256, 0, s>>>(G, S, O.list, O.count, O.cap);
-            else k_rt_overflow<false><<<(unsigned)sms * 2, 256, 0, s>>>(G, S, O.list, O.count, O.cap);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
         done += m;
     }
     return cudaSuccess;
