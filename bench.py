@@ -37,12 +37,11 @@ METRIC = "packets/sec (Gpps) cube update + end-of-window detect ms; fraction of 
 
 
 def update_kernels(partitioned: bool, tuning: dict, n: int) -> int:
-    """Kernels of one update call: direct 1; row tiles count, scan, scatter, apply, plus the
-    overflow pass when run capacities come from a sample (tile_kind 3, or 0 for >= 8Mi packets)."""
-    if not partitioned:
-        return 1
-    k = tuning.get("tile_kind", 0)
-    return 5 if k == 3 or (k == 0 and n >= (8 << 20)) else 4
+    """Kernels of one update call: direct 1; partitioned count, scan, scatter, apply (with sampled
+    run capacities the apply also drains the overflow list).  One pass of up to the workspace's
+    packets; tuning and n are kept for the call sites' clarity."""
+    del tuning, n
+    return 4 if partitioned else 1
 
 
 def detect_kernels(geo: dict) -> int:
