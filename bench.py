@@ -599,6 +599,119 @@ def run_sharded(args):
     return 0
 
 
+def eq2_eq3(detected, ips, cnt, theta):
+    """FNR and FPR of Section V.B (Eq. 2, Eq. 3): H = hosts with >= theta peers; false positives are
+    detected addresses with fewer than theta peers (0 for addresses never seen); both over |H|."""
+    card = dict(zip(ips.tolist(), cnt.tolist()))
+    H = {ip for ip, c in card.items() if c >= theta}
+    D = set(np.asarray(detected).tolist())
+    fp = sum(1 for ip in D if card.get(ip, 0) < theta)
+    return len(H - D) / max(1, len(H)), fp / max(1, len(H)), len(H)
+
+
+def run_learned(args):
+    """Learned estimator on a saturated cube (16M-packet windows of the 64M shape in a 4 MiB cube,
+    ~1.4 g flows per column): GPU training throughput of the library's gradient and Adam kernels,
+    feature + inference + decision time per candidate, and Eq. 2 / Eq. 3 of Thm. 2 alone against the
+    learned decision on a held-out window.  Exact cardinalities are counted on the device
+    (torch.unique of the distinct pairs): measurement, not the detector's path."""
+    import torch
+    from paper_1901_06207_b300 import cbaa as C
+    from paper_1901_06207_b300 import learned as L
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    geo, theta = C.make_params(5, 3, 1, 8, [10]), 256
+
+    def window(seed):
+        w = T.make_window(T.spec_window_64m(seed=seed, scale_shift=2))
+        pairs = torch.from_numpy(w.pairs.view(np.int32)).to(dev)
+        cube = C.Cube(geo, device=dev)
+        cube.update_binned(pairs, C.UpdateWorkspace(geo, pairs.shape[0], device=dev))
+        key = ((pairs[:, 0].to(torch.int64) & 0xFFFFFFFF) << 32) | (pairs[:, 1].to(torch.int64) & 0xFFFFFFFF)
+        src = (torch.unique(key) >> 32) & 0xFFFFFFFF
+        ips, cnt = torch.unique_consecutive(src, return_counts=True)
+        ips, cnt = ips.cpu().numpy().astype(np.uint32), cnt.cpu().numpy()
+        cand = cube.detect(theta // 2)["ip"].astype(np.uint32)
+        pos = np.minimum(np.searchsorted(ips, cand), ips.size - 1)
+        truth = np.where(ips[pos] == cand, cnt[pos], 0)
+        return cube, cand, truth, ips, cnt
+
+    cube_tr, cand_tr, truth_tr, _, _ = window(0xC0FFEE41)
+    cube_te, cand_te, truth_te, ips_te, cnt_te = window(0xC0FFEE40)
+    Xtr = L.features(cube_tr, theta, torch.from_numpy(cand_tr.view(np.int32)).to(dev))
+    idx = torch.from_numpy(L.LearnedEstimator.balanced_indices(truth_tr)).to(dev)
+    X = Xtr[idx].contiguous()
+    t = L.LearnedEstimator.target(X, torch.from_numpy(truth_tr.astype(np.float32)).to(dev)[idx])
+    net = L.LearnedEstimator(device=dev, seed=7)
+    epochs, batch = 40, 1 << 12
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.train(X, t, epochs=epochs, batch=batch, lr=3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # the gradient + Adam kernels alone, on one batch, CUDA events
+    xb, tb = X[:batch].contiguous(), t[:batch].contiguous()
+    probe = L.LearnedEstimator(device=dev, seed=8)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        probe.loss_grad(xb, tb, scale=1.0 / batch)
+        probe.adam(lr=1e-6)
+    reps = 200
+    e0.record(stream)
+    for _ in range(reps):
+        probe.loss_grad(xb, tb, scale=1.0 / batch)
+        probe.adam(lr=1e-6)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / reps
+    # inference on the held-out candidates: features, forward, decision
+    cand_dev = torch.from_numpy(cand_te.view(np.int32)).to(dev)
+    for _ in range(3):
+        Xte = L.features(cube_te, theta, cand_dev)
+        card, dec = net.decide(net.predict(Xte), Xte, geo["log2_g"], theta)
+    e0.record(stream)
+    for _ in range(20):
+        Xte = L.features(cube_te, theta, cand_dev)
+        card, dec = net.decide(net.predict(Xte), Xte, geo["log2_g"], theta)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1) / 20
+    dec = dec.cpu().numpy().astype(bool)
+    plain = cube_te.detect(theta)["ip"]
+    fnr_p, fpr_p, nH = eq2_eq3(plain, ips_te, cnt_te, theta)
+    fnr_l, fpr_l, _ = eq2_eq3(cand_te[dec], ips_te, cnt_te, theta)
+    flop_per_sample = 3 * 2 * (16 * 64 + 64 * 64 + 64)          # forward + backward multiply-adds, x2 flops
+    achieved = flop_per_sample * batch / (step_ms * 1e-3)
+    peak_fp32 = 148 * 128 * 2 * 2.032e9                          # SMs x FP32 lanes x FMA x max clock
+    line = {"metric": "learned estimator: FNR + FPR (Eq. 2, Eq. 3) on a held-out saturated window",
+            "value": fnr_l + fpr_l, "unit": "fraction of |H|", "n_gpus": world, "steps": epochs, "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights, fp32",
+            "data": "synthetic",
+            "config": {"workload": "learned_saturated_16m", "geometry": "r=5, |RA|=3, |VA|=1, g=2^8, c=2^10 (4 MiB)",
+                       "theta": theta, "candidates": "restored at theta/2", "train_seed": "0xC0FFEE41",
+                       "test_seed": "0xC0FFEE40", "network": "16-64-64-1, residual on ln(1 + Thm. 2 estimate)"},
+            "hosts_H": nH, "thm2": {"fnr": fnr_p, "fpr": fpr_p}, "learned": {"fnr": fnr_l, "fpr": fpr_l},
+            "candidates_test": int(cand_te.size), "train_samples": int(X.shape[0]),
+            "train_s_api": train_s, "train_loss_first_last": [losses[0], losses[-1]],
+            "step_ms_batch": step_ms, "train_samples_per_s": batch / (step_ms * 1e-3),
+            "inference_ms_all_candidates": infer_ms,
+            "inference_ns_per_candidate": infer_ms * 1e6 / max(1, cand_te.size),
+            "roofline": {"bound": "alu", "kernel": "cbaa_mlp_grad + cbaa_mlp_adam (one batch)",
+                         "achieved": achieved / 1e12, "peak": peak_fp32 / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp32,
+                         "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (nominal, CUDA cores)"},
+            "gpu_launches": reps * 2}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def _router_window_job(args):
     seed, n_routers = args
     spec = T.spec_window_64m(seed=seed, scale_shift=2)
@@ -800,7 +913,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cbaa", "reference"], default="cbaa")
     ap.add_argument("--workload", default="window64m",
-                    choices=["window64m", "window1m", "batched", "serve", "sharded"])
+                    choices=["window64m", "window1m", "batched", "serve", "sharded", "learned"])
     ap.add_argument("--serve-rate", type=float, default=2e8, help="serve workload: offered packets/s")
     ap.add_argument("--serve-window-s", type=float, default=1.0, help="serve workload: window length")
     ap.add_argument("--serve-windows", type=int, default=3, help="serve workload: windows per run")
@@ -825,6 +938,8 @@ def main():
         return run_serve(args)
     if args.workload == "sharded":
         return run_sharded(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_cbaa(args)
 
 
