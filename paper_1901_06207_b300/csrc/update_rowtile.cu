@@ -594,7 +594,9 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
     uint64_t max_sampled = 0;
     if (T.tile_kind == 3 || (T.tile_kind == 0 && n >= kMinSampled)) {
         max_sampled = sampled_pass_max(G, W, nb, rec_words, n);
-        const uint64_t least = T.tile_kind == 3 ? (n < (1u << 16) ? n : (1u << 16)) : kMinSampled;
+        // kind 3: any pass of a useful size; kind 0: only where it takes no more passes than counting
+        const uint64_t counted = n < max_pairs ? n : max_pairs;
+        const uint64_t least = T.tile_kind == 3 ? (n < (1u << 16) ? n : (1u << 16)) : counted;
         if (max_sampled < least) max_sampled = 0;
     }
     const bool sampled = max_sampled > 0;
