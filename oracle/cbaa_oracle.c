@@ -1,13 +1,17 @@
 /*
  * CBAA CPU oracle -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded restatement of the Cube of Bit Arrays
+ * A plain, slow restatement of the Cube of Bit Arrays
  * Algorithm of Xu, Ding and Hu, "GPU based Real-time Super Hosts Detection at
  * Distributed Edge Routers" (arXiv 1901.06207).  Only the test suite, the
  * smoke check and the benchmark's CPU-baseline leg may load this file; the
  * product path never does.  It shares no code, header, table or constant
  * generator with the CUDA library: everything below is written out again
  * from the paper.
+ *
+ * The cube is built one pair at a time (oracle_update) or by OpenMP threads
+ * on private cubes that are OR-ed afterwards (oracle_update_threads); the
+ * brute-force restoration check also runs on OpenMP threads.
  *
  * Each function names the passage it follows.  Where the paper is silent or
  * garbled the reading used is stated at the function.  Floating point is
@@ -228,6 +232,41 @@ void oracle_merge(uint32_t *dst, const uint32_t *src, uint64_t words)
 {
     for (uint64_t w = 0; w < words; ++w)
         dst[w] |= src[w];
+}
+
+/* Alg. 1 run by nthreads threads, each on a private cube built from its own
+ * contiguous share of the pairs, the private cubes then OR-ed into `cube`
+ * (the multi-router model of Section III.C: every router keeps a cube of the
+ * same structure and the global cube is their OR).  Alg. 1 only sets bits, so
+ * the result equals oracle_update over all n pairs for any split; the test
+ * suite checks exactly that, which makes this both a second build mode and a
+ * merge test.  `cube` may already hold bits; they are kept. */
+int oracle_update_threads(const oracle_geometry *G, uint32_t *cube, const uint32_t *pairs, uint64_t n,
+                          int nthreads)
+{
+    uint64_t words = oracle_cube_words(G);
+    if (nthreads < 1) nthreads = 1;
+    uint32_t **priv = (uint32_t **)calloc((size_t)nthreads, sizeof(uint32_t *));
+    if (!priv) return -1;
+    int ok = 1;
+    for (int t = 0; t < nthreads; ++t) {
+        priv[t] = (uint32_t *)calloc((size_t)words, sizeof(uint32_t));
+        if (!priv[t]) ok = 0;
+    }
+    if (ok) {
+#pragma omp parallel for num_threads(nthreads) schedule(static, 1)
+        for (int t = 0; t < nthreads; ++t) {
+            uint64_t lo = n * (uint64_t)t / (uint64_t)nthreads;
+            uint64_t hi = n * (uint64_t)(t + 1) / (uint64_t)nthreads;
+            oracle_update(G, priv[t], pairs + 2 * lo, hi - lo);
+        }
+        for (int t = 0; t < nthreads; ++t)
+            oracle_merge(cube, priv[t], words);
+    }
+    for (int t = 0; t < nthreads; ++t)
+        free(priv[t]);
+    free(priv);
+    return ok ? 0 : -1;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -78,6 +78,7 @@ def lib():
             "oracle_cube_words": (ctypes.c_uint64, [G]),
             "oracle_update": (None, [G, u32p, u32p, ctypes.c_uint64]),
             "oracle_merge": (None, [u32p, u32p, ctypes.c_uint64]),
+            "oracle_update_threads": (ctypes.c_int, [G, u32p, u32p, ctypes.c_uint64, ctypes.c_int]),
             "oracle_zero_counts": (None, [G, u32p, u32p, u64p]),
             "oracle_eps": (ctypes.c_double, [G, u64p, ctypes.c_uint32]),
             "oracle_exp_factor": (ctypes.c_double, [ctypes.c_uint32, ctypes.c_uint32]),
@@ -152,6 +153,18 @@ def update(d, cube: np.ndarray, pairs: np.ndarray) -> np.ndarray:
 
 def build_cube(d, pairs: np.ndarray) -> np.ndarray:
     return update(d, new_cube(d), pairs)
+
+
+def update_threads(d, cube: np.ndarray, pairs: np.ndarray, nthreads: int) -> np.ndarray:
+    """Alg. 1 on `nthreads` private cubes (one contiguous share of the pairs each), OR-ed into `cube`
+    as the global cube of Section III.C is formed from same-structure router cubes."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32)
+    assert cube.dtype == np.uint32 and cube.size == cube_words(d)
+    rc = lib().oracle_update_threads(_G(d), _p(cube, ctypes.c_uint32), _p(pairs, ctypes.c_uint32),
+                                     pairs.shape[0], int(nthreads))
+    if rc != 0:
+        raise MemoryError(f"oracle_update_threads: {nthreads} private cubes did not fit in host memory")
+    return cube
 
 
 def merge(dst: np.ndarray, src: np.ndarray) -> np.ndarray:

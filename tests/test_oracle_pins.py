@@ -160,6 +160,21 @@ def test_merge_homomorphism(oracle):
     assert not zero.any()
 
 
+@pytest.mark.parametrize("nthreads", [1, 2, 3, 8])
+def test_threaded_build_is_a_merge(oracle, nthreads):
+    """The threaded build ORs private cubes of contiguous shares; Alg. 1 only sets bits, so any split
+    gives the one-pair-at-a-time cube, including shares that are empty (n < threads) and bits already set."""
+    d = GEO.TINY2
+    w = _tiny_window(17)
+    whole = oracle.build_cube(d, w.pairs)
+    assert np.array_equal(oracle.update_threads(d, oracle.new_cube(d), w.pairs, nthreads), whole)
+    few = w.pairs[:5]
+    assert np.array_equal(oracle.update_threads(d, oracle.new_cube(d), few, nthreads), oracle.build_cube(d, few))
+    head, tail = w.pairs[: len(w.pairs) // 3], w.pairs[len(w.pairs) // 3:]
+    assert np.array_equal(oracle.update_threads(d, oracle.build_cube(d, head), tail, nthreads), whole)
+    assert not oracle.update_threads(d, oracle.new_cube(d), w.pairs[:0], nthreads).any()
+
+
 # ------------------------------------------------------------------ zero counts, Thm. 1, theta_bn
 
 def test_zero_counts_match_popcount(oracle):
