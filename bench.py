@@ -212,13 +212,35 @@ def _cpu_model():
     return None
 
 
+def oracle_threads_sample(geo, pairs: np.ndarray, n_sample: int, threads: int):
+    """Time the oracle's OpenMP build (private cubes OR-ed) on the same sample; checks it against the
+    single-threaded cube so the number belongs to a correct build."""
+    from oracle import oracle as O
+    sample = np.ascontiguousarray(pairs[:n_sample])
+    t0 = time.perf_counter()
+    cube = O.update_threads(geo, O.new_cube(geo), sample, threads)
+    t1 = time.perf_counter()
+    same = bool(np.array_equal(cube, O.build_cube(geo, sample)))
+    return {"update_s": t1 - t0, "same_cube": same}
+
+
 def cpu_baseline(geo, pairs, theta, n_sample):
     r = oracle_sample(geo, pairs, theta, n_sample)
     v = r["packets"] / (r["update_s"] + r["detect_s"]) / 1e9
-    return {"value": v, "unit": "Gpps", "cores": 1, "kind": "oracle",
-            "sample": f"first {r['packets']} packets of the window (Alg. 1) + one full detect of that cube; "
-                      f"update {r['update_s']:.3f} s, detect {r['detect_s']:.3f} s, single-threaded C",
-            "cpu": _cpu_model(), "host_cores": os.cpu_count()}
+    out = {"value": v, "unit": "Gpps", "cores": 1, "kind": "oracle",
+           "sample": f"first {r['packets']} packets of the window (Alg. 1) + one full detect of that cube; "
+                     f"update {r['update_s']:.3f} s, detect {r['detect_s']:.3f} s, single-threaded C",
+           "update_gpps": r["packets"] / r["update_s"] / 1e9, "detect_ms": 1e3 * r["detect_s"],
+           "cpu": _cpu_model(), "host_cores": os.cpu_count()}
+    threads = max(1, min(os.cpu_count() or 1, 32))
+    if threads > 1:
+        t = oracle_threads_sample(geo, pairs, n_sample, threads)
+        out["openmp"] = {"cores": threads, "update_gpps": r["packets"] / t["update_s"] / 1e9,
+                         "value": r["packets"] / (t["update_s"] + r["detect_s"]) / 1e9, "unit": "Gpps",
+                         "same_cube": t["same_cube"],
+                         "sample": f"same packets on {threads} OpenMP threads, one private cube each, OR-ed; "
+                                   f"update {t['update_s']:.3f} s, the single-threaded detect above"}
+    return out
 
 
 def run_reference(args):

@@ -260,8 +260,11 @@ int oracle_update_threads(const oracle_geometry *G, uint32_t *cube, const uint32
             uint64_t hi = n * (uint64_t)(t + 1) / (uint64_t)nthreads;
             oracle_update(G, priv[t], pairs + 2 * lo, hi - lo);
         }
-        for (int t = 0; t < nthreads; ++t)
-            oracle_merge(cube, priv[t], words);
+        /* the OR of Section III.C, word by word, the words split across the threads */
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+        for (int64_t w = 0; w < (int64_t)words; ++w)
+            for (int t = 0; t < nthreads; ++t)
+                cube[w] |= priv[t][w];
     }
     for (int t = 0; t < nthreads; ++t)
         free(priv[t]);
