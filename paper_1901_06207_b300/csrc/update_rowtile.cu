@@ -389,10 +389,14 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
                                                             const uint32_t *__restrict__ cursors,
                                                             const uint2 *__restrict__ ovf,
                                                             const uint32_t *__restrict__ ovf_count, uint32_t ovf_cap) {
-    extern __shared__ uint32_t tile[];
+    extern __shared__ __align__(16) uint32_t tile[];
     __shared__ uint32_t s_item;
     const uint32_t items = item_start[nb];
     const uint32_t tiles_per_router = (G.smask + 1) * G.W;
+    uint4 *tile4 = reinterpret_cast<uint4 *>(tile);
+    const uint32_t quads = tile_words / 4;             // arrays start at multiples of 32 words
+    // zeroed once: each flush leaves the words it read zero again
+    for (uint32_t q = threadIdx.x; q < quads; q += blockDim.x) tile4[q] = make_uint4(0u, 0u, 0u, 0u);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
         __syncthreads();
@@ -412,8 +416,6 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
             __syncthreads();                              // s_item is read by every thread first
             continue;
         }
-        for (uint32_t i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0;
-        __syncthreads();
         uint32_t c = c0 + threadIdx.x;
         for (; c + 3 * blockDim.x < c1; c += 4 * blockDim.x) {        // four records in flight
             Rec rv[4];
@@ -428,13 +430,19 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
         const uint32_t rem = b - router * tiles_per_router;
         const uint32_t cs = rem / G.W, w = rem - cs * G.W;
         uint32_t *cube = S.cube[router] + (size_t)cs * G.cs_words + w;
-        for (uint32_t t = threadIdx.x; t < tile_words; t += blockDim.x) {
-            const uint32_t v = tile[t];
-            if (!v) continue;
-            uint32_t a = 0;                                   // array of tile word t
+        // four tile words (four consecutive columns of one array) per step
+        for (uint32_t q = threadIdx.x; q < quads; q += blockDim.x) {
+            const uint4 v = tile4[q];
+            if (!(v.x | v.y | v.z | v.w)) continue;
+            const uint32_t t = 4 * q;
+            uint32_t a = 0;                                   // array of tile words t .. t+3
             while (a + 1 < G.A && t >= G.col_base[a + 1]) ++a;
-            const uint32_t col = t - G.col_base[a];
-            red_or(cube + G.arr_base[a] + (size_t)col * G.W, v);
+            uint32_t *dst = cube + G.arr_base[a] + (size_t)(t - G.col_base[a]) * G.W;
+            if (v.x) red_or(dst, v.x);
+            if (v.y) red_or(dst + G.W, v.y);
+            if (v.z) red_or(dst + 2 * G.W, v.z);
+            if (v.w) red_or(dst + 3 * G.W, v.w);
+            tile4[q] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();
     }

@@ -57,3 +57,40 @@ def test_graph_batched_windows_match_oracle_and_plain(C, oracle):
     bounds = np.concatenate([[0], np.cumsum(counts)])
     for j in range(R):
         assert np.array_equal(rw.routers[j].to_numpy(), oracle.build_cube(d, pairs[bounds[j]:bounds[j + 1]]))
+
+
+def test_full_size_router_windows(C, oracle):
+    """The batched benchmark's configuration: 16M-packet windows of the 64M shape over 8 routers with
+    lognormal loads, the L2 geometry, the tuned tiling, one graph; every window's host list and the
+    last window's router cubes against the oracle (4 windows: both global buffers, twice)."""
+    import os
+    import torch
+    from paper_1901_06207_b300.batch import RouterWindows
+    d, theta, R = GEO.L2, 1024, 8
+    wins = [T.router_window(T.spec_window_64m(seed=0xC0FFEE20 + w, scale_shift=2), R)[:2] for w in range(4)]
+    dev = []
+    for pairs, counts in wins:
+        p = torch.from_numpy(pairs.view(np.int32)).cuda()
+        b = np.concatenate([[0], np.cumsum(counts)])
+        dev.append([p[b[j]:b[j + 1]] if counts[j] else None for j in range(R)])
+    base = C.get_tuning()
+    try:
+        rw = RouterWindows(d, R, theta, max_pairs=max(int(c.sum()) for _, c in wins), n_windows=len(wins))
+        rw.tune(dev)
+        rw.capture(dev)
+        rw.replay()
+        res = rw.results()
+    finally:
+        C.set_tuning(**base)
+    threads = max(1, min(os.cpu_count() or 1, 16))
+    for w, (pairs, counts) in enumerate(wins):
+        hosts, info = res[w]
+        assert info["status"] == C.OK
+        want = oracle.detect(d, oracle.update_threads(d, oracle.new_cube(d), pairs, threads), theta)["hosts"]
+        assert hosts.size == want.size and np.array_equal(hosts["ip"], want["ip"])
+        assert np.array_equal(hosts["z"], want["z"]) and np.array_equal(hosts["flags"], want["flags"])
+        assert np.allclose(hosts["est"], want["est"], rtol=1e-6)
+    pairs, counts = wins[-1]
+    b = np.concatenate([[0], np.cumsum(counts)])
+    for j in range(R):
+        assert np.array_equal(rw.routers[j].to_numpy(), oracle.build_cube(d, pairs[b[j]:b[j + 1]]))

@@ -368,3 +368,18 @@ def test_full_size_64m_window(C, oracle):
     want = oracle.detect(d, want_cube, 1024)["hosts"]
     assert_hosts_equal(got, want)
     assert set(w.planted_ips.tolist()) <= set(got["ip"].tolist())
+    # the benchmark's own launch configuration: the autotuner's pick over every path and shape
+    from paper_1901_06207_b300 import autotune
+    base = C.get_tuning()
+    try:
+        pairs = dev_pairs(w.pairs)
+        tuned = autotune.tune_update(d, pairs, use_cache=False)
+        cube.reset()
+        if tuned["path"] == "binned":
+            cube.update_binned(pairs, C.UpdateWorkspace(d, pairs.shape[0]))
+        else:
+            cube.update(pairs)
+        assert np.array_equal(cube.to_numpy(), want_cube), tuned["tuning"]
+        assert_hosts_equal(cube.detect(1024), want)
+    finally:
+        C.set_tuning(**base)
