@@ -549,7 +549,7 @@ def run_cbaa(args):
                                             "measured in this run"}},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(geo, w.pairs, theta, min(n, args.reference_sample))
+        line["cpu_baseline"] = cpu_baseline(geo, w.pairs, theta, min(n, args.cpu_sample or n))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -948,6 +948,8 @@ def main():
     ap.add_argument("--routers", type=int, default=8, help="batched workload: simulated edge routers")
     ap.add_argument("--reference-sample", type=int, default=4 << 20,
                     help="packets per CPU-oracle step (bounded sample of the window)")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="packets of the window the cpu_baseline oracle run takes (0: the whole window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "cbaa":
