@@ -271,14 +271,27 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU leg
 
+def source_digest(rel: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def load_traffic(workload_name: str, path: str):
-    """DRAM bytes of one window's update from the committed ncu summary, if it is current."""
+    """DRAM bytes of one window's update from the committed ncu summary, or None when the summary is
+    missing or any kernel source it lists has changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", f"update_{path}_{workload_name}.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            d = json.load(f)
-        return d.get("dram_bytes_per_launch")
-    return None
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    srcs = d.get("sources")
+    if not srcs:
+        return None
+    for rel, digest in srcs.items():
+        if not os.path.exists(os.path.join(ROOT, rel)) or source_digest(rel) != digest:
+            return None
+    return d.get("dram_bytes_per_launch")
 
 
 def run_cbaa(args):
