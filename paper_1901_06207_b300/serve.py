@@ -11,7 +11,9 @@ networks) at once:
 * Requests (host batches of pairs) are admitted as soon as a staging
   slot is free and their window holds a cube, so the copy of one batch,
   the update of another and the detect of a closed window overlap on the
-  device (copy stream, compute stream, detect stream).
+  device (copy stream, compute stream, detect stream).  Batches of the
+  same window already queued behind an admitted one join it in its slot
+  while they fit: one copy each, one update for all.
 * Window cubes come from a pool sized by a device-memory budget; a new
   window waits (its batches stay queued) until a cube is free again.  At
   most two cubes per tenant are in use (double buffering: one filling,
@@ -79,7 +81,7 @@ class _Open:
 class Server:
     def __init__(self, geo: dict, theta: int, *, n_slots: int = 4, slot_pairs: int = 1 << 22,
                  mem_budget: int | None = None, n_cubes: int | None = None, max_candidates: int = 1 << 18,
-                 cap: int = 1 << 14, device="cuda"):
+                 cap: int = 1 << 14, lookahead: int = 64, device="cuda"):
         torch = C._torch()
         self.geo, self.theta, self.cap, self.device = dict(geo), theta, cap, device
         self.cube_bytes = C.cube_bytes(geo)
@@ -108,21 +110,26 @@ class Server:
         self.closing = collections.deque()      # (tenant, _Open, close_t) waiting for a cube-free detect slot
         self.detecting = collections.deque()    # (tenant, _Open, close_t, done_event, host_out, host_info)
         self.results = []
-        self.stats = dict(admitted=0, queued_for_cube=0, queued_for_slot=0, max_cubes_in_use=0, batches=0)
+        self.stats = dict(admitted=0, queued_for_cube=0, queued_for_slot=0, max_cubes_in_use=0, batches=0,
+                          updates=0)
+        self.lookahead = lookahead
 
     # ------------------------------------------------------------------ public API
-    def submit(self, tenant, window: int, pairs, arrival_t: float | None = None):
-        """Queue a batch (host int32/uint32 [n, 2] tensor, ideally pinned) for tenant's window."""
+    def submit(self, tenant, window: int, pairs, arrival_t: float | None = None, poll: bool = True):
+        """Queue a batch (host int32/uint32 [n, 2] tensor, ideally pinned) for tenant's window.
+        poll=False only queues it (a burst submitted at once is admitted by the next poll)."""
         n = int(pairs.shape[0])
         if n > self.slot_pairs:
             raise C.CbaaError(C.ERR_INVALID_ARG, f"batch of {n} pairs exceeds the slot size {self.slot_pairs}")
         self.queue.append(_Request(tenant, window, pairs, n, time.perf_counter() if arrival_t is None else arrival_t))
-        self.poll()
+        if poll:
+            self.poll()
 
-    def close(self, tenant, window: int):
+    def close(self, tenant, window: int, poll: bool = True):
         """Mark tenant's window complete: its detect runs once its queued batches are in."""
         self.queue.append(_Request(tenant, window, None, -1, time.perf_counter()))
-        self.poll()
+        if poll:
+            self.poll()
 
     def poll(self):
         """Advance: retire finished work, admit queued requests, start detects."""
@@ -186,19 +193,44 @@ class Server:
                 pending.append(r)
                 continue
             slot.busy = True
+            group = [r] + self._absorb(r)
             with torch.cuda.stream(self.copy_s):
-                slot.stage[:r.n].copy_(r.pairs, non_blocking=True)
+                off = 0
+                for q in group:
+                    slot.stage[off:off + q.n].copy_(q.pairs, non_blocking=True)
+                    off += q.n
                 copied = torch.cuda.Event()
                 copied.record(self.copy_s)
             self.comp_s.wait_event(copied)
-            cur.cube.update_binned(slot.stage, slot.uws, n=r.n, stream=self.comp_s)
+            cur.cube.update_binned(slot.stage, slot.uws, n=off, stream=self.comp_s)
             slot.done = torch.cuda.Event()
             slot.done.record(self.comp_s)
             cur.last = slot.done
-            cur.packets += r.n
-            self.stats["admitted"] += 1
-            self.stats["batches"] += 1
+            cur.packets += off
+            self.stats["admitted"] += len(group)
+            self.stats["batches"] += len(group)
+            self.stats["updates"] += 1
         self.queue = pending
+
+    def _absorb(self, r):
+        """Later queued batches of r's tenant and window that fill r's slot with it (one copy each, one
+        update for all): the tenant's next requests in order, up to the first that is of another window,
+        a close marker or too large, looking at most `lookahead` requests ahead."""
+        taken, room, keep = [], self.slot_pairs - r.n, []
+        for i, q in enumerate(self.queue):
+            if i >= self.lookahead:
+                break
+            if q.tenant != r.tenant:
+                continue
+            if q.n < 0 or q.window != r.window or q.n > room:
+                break
+            taken.append(q)
+            keep.append(i)
+            room -= q.n
+        if keep:
+            drop = set(keep)
+            self.queue = collections.deque(q for i, q in enumerate(self.queue) if i not in drop)
+        return taken
 
     def _start_detects(self):
         torch = C._torch()

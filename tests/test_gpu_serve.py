@@ -82,6 +82,25 @@ def test_serving_results_same_alone_and_mixed(C, oracle):
     assert srv.stats["queued_for_cube"] > 0
 
 
+def test_queued_batches_share_a_slot_update(C, oracle):
+    """A burst queued at once: batches of one window join the admitted one in its slot while they fit
+    (one update for several batches), never across a window's close; results equal the oracle's."""
+    from paper_1901_06207_b300.serve import Server
+    srv = Server(GEO.TINY2, THETA, n_slots=2, slot_pairs=1 << 16, n_cubes=2, cap=1 << 12)
+    for w in range(2):
+        for b in _batches(_traffic(0, w), 900 + w):
+            srv.submit(0, w, _pinned(b), poll=False)
+        srv.close(0, w, poll=False)
+    res = {r.window: r for r in srv.drain(timeout_s=120)}
+    assert set(res) == {0, 1}
+    assert srv.stats["updates"] < srv.stats["batches"]
+    for w in range(2):
+        pairs = _traffic(0, w)
+        assert res[w].packets == pairs.shape[0] and res[w].info["status"] == C.OK
+        want = oracle.detect(GEO.TINY2, oracle.build_cube(GEO.TINY2, pairs), THETA)["hosts"]
+        assert np.array_equal(res[w].hosts["ip"], want["ip"]) and np.array_equal(res[w].hosts["z"], want["z"])
+
+
 def test_serving_budget_and_batch_limits(C):
     from paper_1901_06207_b300.serve import Server
     with pytest.raises(C.CbaaError):
