@@ -828,6 +828,14 @@ def run_batched(args):
     hosts_last, _ = C.hosts_from_device(out, info)
     assert np.array_equal(hosts_last, res[-1][0]), "plain and batched host lists differ"
     plain_value = total_packets * steps / (plain_ms * 1e-3) / 1e9
+
+    # the OR merge of Section III.C alone (a6): the 8 router cubes of the last window into a global cube;
+    # algorithmic bytes = every router cube read + the global cube read and written
+    merge_reps = 20
+    merge_ms = timed(lambda: rw.globs[0].merge(rw.routers), merge_reps) / merge_reps
+    merge_bytes = (R + 2) * C.cube_bytes(geo)
+    hbm_peak, hbm_src = measured_peaks()
+    merge_gbs = merge_bytes / (merge_ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -842,6 +850,10 @@ def run_batched(args):
             "window_ms": ms / steps / len(wins), "router_update_tiling": tiling,
             "plain_single_cube": {"value": plain_value, "unit": "Gpps", "window_ms": plain_ms / steps / len(wins),
                                   "path": "one cube, partitioned update of the whole window, detect, no graph"},
+            "merge": {"ms": merge_ms, "sources": R, "bytes": merge_bytes,
+                      "roofline": {"bound": "hbm", "kernel": "k_merge", "achieved": merge_gbs, "peak": hbm_peak,
+                                   "unit": "GB/s", "frac": merge_gbs / hbm_peak,
+                                   "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}},
             "hosts_per_window": [int(i["n_hosts"]) for _, i in res],
             "gpu_launches": steps * len(wins) * (update_kernels(True, C.get_tuning(), sum(n_per) // len(wins)) + 1 +
                                                  detect_kernels(geo)),

@@ -96,14 +96,19 @@ struct SrcList {
     int k;
 };
 
+// Every source's 16 bytes are loaded before the first OR, so a thread keeps
+// L.k + 1 loads in flight.
 __global__ void __launch_bounds__(256) k_merge(uint4 *__restrict__ dst, const SrcList L, uint64_t n16) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        uint4 b[kMaxSrc];
+#pragma unroll
+        for (int k = 0; k < kMaxSrc; ++k)
+            if (k < L.k) b[k] = ld_stream(L.p[k] + i);
         uint4 a = dst[i];
-        for (int k = 0; k < L.k; ++k) {
-            const uint4 b = ld_stream(L.p[k] + i);
-            a.x |= b.x; a.y |= b.y; a.z |= b.z; a.w |= b.w;
-        }
+#pragma unroll
+        for (int k = 0; k < kMaxSrc; ++k)
+            if (k < L.k) { a.x |= b[k].x; a.y |= b[k].y; a.z |= b[k].z; a.w |= b[k].w; }
         dst[i] = a;
     }
 }
