@@ -34,7 +34,7 @@ def _dev(pairs):
 
 
 @pytest.mark.parametrize("geo", ["L2", "PAPER", "DUO"])
-@pytest.mark.parametrize("path", ["direct", "kind1", "kind2"])
+@pytest.mark.parametrize("path", ["direct", "kind1", "kind2", "kind3"])
 def test_oriented_cube_equals_oracle(C, oracle, raw, geo, path):
     d = GEO.ALL[geo]
     before = C.get_tuning()
@@ -44,7 +44,7 @@ def test_oriented_cube_equals_oracle(C, oracle, raw, geo, path):
         if path == "direct":
             cube.update(_dev(raw))
         else:
-            C.set_tuning(**{**before, "tile_kind": 1 if path == "kind1" else 2})
+            C.set_tuning(**{**before, "tile_kind": int(path[-1])})     # kind3: sampled run capacities
             cube.update_binned(_dev(raw), C.UpdateWorkspace(d, raw.shape[0]))
         assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, oracle.orient(raw, NI)))
     finally:

@@ -108,3 +108,31 @@ def test_serving_budget_and_batch_limits(C):
     srv = Server(GEO.TINY2, THETA, n_slots=1, slot_pairs=1 << 10, n_cubes=1)
     with pytest.raises(C.CbaaError):
         srv.submit(0, 0, _pinned(np.zeros((2048, 2), np.uint32)))                     # larger than a slot
+
+
+def test_full_size_serving_window(C, oracle):
+    """The serving benchmark's configuration: the 64M-packet window of the core-network shape cut into
+    batches log-uniform in [64Ki, 4Mi] pairs, served into the 256 MiB geometry (r=6, c=2^13) by 4 staging
+    slots of 4Mi pairs and 4 cubes as one window; host list against the oracle's."""
+    import os
+    import torch
+    from paper_1901_06207_b300.serve import Server
+    d, theta = GEO.SERVE, 1024
+    pairs = T.make_window(T.spec_window_64m(seed=0xC0FFEE30)).pairs
+    pool = torch.from_numpy(pairs.view(np.int32)).pin_memory()
+    rng = np.random.default_rng(0x5E7E)
+    srv = Server(d, theta, n_slots=4, slot_pairs=4 << 20, n_cubes=4)
+    off = 0
+    while off < pairs.shape[0]:
+        n = int(np.exp(rng.uniform(np.log(1 << 16), np.log(4 << 20))))
+        srv.submit(0, 0, pool[off:off + n])
+        off += n
+    srv.close(0, 0)
+    res = srv.drain(timeout_s=300)
+    assert len(res) == 1 and res[0].packets == pairs.shape[0] and res[0].info["status"] == C.OK
+    threads = max(1, min(os.cpu_count() or 1, 8))                # 8 private 256 MiB cubes on the host
+    want = oracle.detect(d, oracle.update_threads(d, oracle.new_cube(d), pairs, threads), theta)["hosts"]
+    got = res[0].hosts
+    assert got.size == want.size and got.size > 0
+    assert np.array_equal(got["ip"], want["ip"]) and np.array_equal(got["z"], want["z"])
+    assert np.array_equal(got["flags"], want["flags"]) and np.allclose(got["est"], want["est"], rtol=1e-6)
