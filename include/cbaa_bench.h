@@ -2,7 +2,7 @@
  * cbaa_bench.h -- measurement helpers exported by libcbaa.so.
  *
  * These calls are not part of the detector.  They measure the hardware
- * roofs that the detector's kernels are judged against.
+ * roofs that the detector's kernels are measured against.
  */
 #ifndef CBAA_BENCH_H
 #define CBAA_BENCH_H
