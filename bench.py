@@ -668,6 +668,9 @@ def run_learned(args):
         src = (torch.unique(key) >> 32) & 0xFFFFFFFF
         ips, cnt = torch.unique_consecutive(src, return_counts=True)
         ips, cnt = ips.cpu().numpy().astype(np.uint32), cnt.cpu().numpy()
+        # the int64 keys of sources >= 2^31 are negative and sort first: restore unsigned order
+        order = np.argsort(ips, kind="stable")
+        ips, cnt = ips[order], cnt[order]
         cand = cube.detect(theta // 2)["ip"].astype(np.uint32)
         pos = np.minimum(np.searchsorted(ips, cand), ips.size - 1)
         truth = np.where(ips[pos] == cand, cnt[pos], 0)
