@@ -57,6 +57,7 @@ Geo make_geo(const cbaa_params &p) {
 }  // namespace cbaa
 
 using cbaa::Geo;
+using cbaa::cuda_status;
 
 namespace {
 
@@ -92,14 +93,6 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 
 thread_local cudaError_t t_last_cuda = cudaSuccess;
 
-// CBAA_OK for cudaSuccess, else CBAA_ERR_CUDA with the error remembered for
-// cbaa_last_cuda_error().
-int cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return CBAA_OK;
-    t_last_cuda = e;
-    return CBAA_ERR_CUDA;
-}
-
 cbaa_tuning g_tuning = {};
 std::mutex g_tuning_mu;
 
@@ -109,6 +102,12 @@ cbaa_tuning current_tuning() {
 }
 
 }  // namespace
+
+int cbaa::cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CBAA_OK;
+    t_last_cuda = e;
+    return CBAA_ERR_CUDA;
+}
 
 extern "C" {
 
@@ -154,9 +153,10 @@ int cbaa_cube_init(const cbaa_params *p, void *dev_mem, size_t bytes, cbaa_cube 
     c->G = G;
     c->data = static_cast<uint32_t *>(dev_mem);
     c->bytes = G.cube_words * 4u;
-    if (cudaMemsetAsync(c->data, 0, c->bytes, as_stream(stream)) != cudaSuccess) {
+    const int st_mem = cuda_status(cudaMemsetAsync(c->data, 0, c->bytes, as_stream(stream)));
+    if (st_mem != CBAA_OK) {
         delete c;
-        return CBAA_ERR_CUDA;
+        return st_mem;
     }
     *out = c;
     return CBAA_OK;
@@ -346,9 +346,9 @@ int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_b
                                   cbaa::num_sms(), s);
     if (st != CBAA_OK) return st;
     cbaa_detect_info info;
-    if (cudaMemcpyAsync(&info, &P.state->info, sizeof info, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return CBAA_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return CBAA_ERR_CUDA;
+    if ((st = cuda_status(cudaMemcpyAsync(&info, &P.state->info, sizeof info, cudaMemcpyDeviceToHost, s))) != CBAA_OK)
+        return st;
+    if ((st = cuda_status(cudaStreamSynchronize(s))) != CBAA_OK) return st;
     if (info.status == CBAA_ERR_WORKSPACE) {
         *n_out = info.need_tuples;
         return CBAA_ERR_WORKSPACE;
@@ -356,9 +356,10 @@ int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_b
     *n_out = info.n_hosts;
     const size_t nw = info.n_hosts < cap ? info.n_hosts : cap;
     if (nw > 0) {
-        if (cudaMemcpyAsync(host_out, P.sorted, nw * sizeof(cbaa_host), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-            return CBAA_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return CBAA_ERR_CUDA;
+        if ((st = cuda_status(cudaMemcpyAsync(host_out, P.sorted, nw * sizeof(cbaa_host), cudaMemcpyDeviceToHost,
+                                              s))) != CBAA_OK)
+            return st;
+        if ((st = cuda_status(cudaStreamSynchronize(s))) != CBAA_OK) return st;
     }
     return info.n_hosts > cap ? CBAA_ERR_CAPACITY : CBAA_OK;
 }

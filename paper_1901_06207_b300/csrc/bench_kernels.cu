@@ -24,5 +24,5 @@ extern "C" int cbaa_bench_red_or(uint32_t *dev_buf, size_t words, size_t n_ops, 
     const unsigned blocks = (unsigned)cbaa::num_sms() * 8;
     k_red_probe<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(dev_buf, (uint32_t)(words - 1), n_ops,
                                                                            seed);
-    return cudaGetLastError() == cudaSuccess ? CBAA_OK : CBAA_ERR_CUDA;
+    return cbaa::cuda_status(cudaGetLastError());
 }

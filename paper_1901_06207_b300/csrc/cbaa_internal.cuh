@@ -129,6 +129,10 @@ __host__ __device__ __forceinline__ uint32_t col_word0(const Geo &G, uint32_t cs
 
 // Host-side launchers implemented in the .cu files.
 namespace cbaa {
+// CBAA_OK for cudaSuccess, else CBAA_ERR_CUDA with the error remembered for
+// cbaa_last_cuda_error() on this host thread.  Every CBAA_ERR_CUDA that the
+// library returns goes through it.
+int cuda_status(cudaError_t e);
 int num_sms();   // SM count of the current device (cached on first use)
 cudaError_t launch_update(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, uint32_t blocks_per_sm,
                           cudaStream_t s);

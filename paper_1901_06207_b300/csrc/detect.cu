@@ -398,11 +398,11 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
     const double E = std::exp(-((double)theta / (double)G.g));
 
     cudaError_t e = cudaMemsetAsync(P.state, 0, sizeof(DevState), s);
-    if (e != cudaSuccess) return CBAA_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s, cs_lo, cs_hi, &P.state->stats_done);
-    if (e != cudaSuccess) return CBAA_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     k_hot_lists<<<dim3(cs_hi - cs_lo, G.n_ra), 1024, 0, s>>>(G, P, cs_lo);
-    if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     const unsigned blocks = (unsigned)num_sms * 4;
     const uint32_t wpl = G.W >= 32 ? G.W / 32 : 1;
     for (uint32_t st = 1; st < G.n_ra; ++st) {
@@ -414,7 +414,7 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
             case 16: e = launch_join<16>(G, cube, P, st, blocks, s); break;
             default: e = launch_join<32>(G, cube, P, st, blocks, s); break;
         }
-        if (e != cudaSuccess) return CBAA_ERR_CUDA;
+        if (e != cudaSuccess) return cuda_status(e);
     }
     cbaa_host *dst = out ? out : P.sorted;
     const uint64_t dcap = out ? cap : P.m;
@@ -422,10 +422,10 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
     const uint64_t per_block = kRankThreads / kRankLanes;
     const uint64_t sort_blocks = (rank_n + per_block - 1) / per_block;
     k_sort<<<(unsigned)(sort_blocks ? sort_blocks : 1), kRankThreads, 0, s>>>(G, P, dst, dcap);
-    if ((e = cudaGetLastError()) != cudaSuccess) return CBAA_ERR_CUDA;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     if (info_copy) {
         e = cudaMemcpyAsync(info_copy, &P.state->info, sizeof(cbaa_detect_info), cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return CBAA_ERR_CUDA;
+        if (e != cudaSuccess) return cuda_status(e);
     }
     return CBAA_OK;
 }

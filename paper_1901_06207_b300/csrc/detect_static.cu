@@ -24,7 +24,9 @@ int scratch_for_current_device(void **out) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_detect_scratch) != cudaSuccess || !p) return CBAA_ERR_CUDA;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_detect_scratch);
+        if (e != cudaSuccess) return cbaa::cuda_status(e);
+        if (!p) return CBAA_ERR_NO_DEVICE;
         g_scratch_addr[dev] = p;
     }
     *out = g_scratch_addr[dev];
