@@ -547,7 +547,13 @@ def run_cbaa(args):
                                "unit": "Gop/s",
                                "frac": 4 * n / (statistics.mean(direct_ms) * 1e-3) / 1e9 / red_peak,
                                "peak_source": "RED.OR microbenchmark on a cube-sized buffer, measured in this run",
-                               "update_ms": statistics.mean(direct_ms)},
+                               "update_ms": statistics.mean(direct_ms),
+                               "chosen_path": {
+                                   "update_gpps": n / upd_s / 1e9, "roof_gpps": red_peak / 4,
+                                   "ratio": n / upd_s / 1e9 / (red_peak / 4),
+                                   "note": "the chosen update against the roof of one L2 RED.OR per bit "
+                                           "(4 per packet); it issues about one reduction per cube word "
+                                           "instead"}},
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_value, "unit": "Gpps", "h2d_bytes_per_step": 8 * n,
