@@ -430,6 +430,35 @@ def run_cbaa(args):
     hosts, inf = C.hosts_from_device(out, info)
     assert inf["status"] == C.OK, inf
 
+    # detect end to end on the last window's cube: window close -> sorted host list in host memory
+    # through the synchronous C call (cbaa_detect: enqueue, wait, copy the list back)
+    det_sync_ms = []
+    for rep in range(21):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs = cube.detect(theta, ws=ws, cap=cap)
+        if rep:
+            det_sync_ms.append(1e3 * (time.perf_counter() - t0))
+    assert hs.size == inf["n_hosts"], (hs.size, inf)
+    # the detect's streaming pass alone (Eq. 1 zero counts, Thm. 1 eps, Zmax: reads the cube once)
+    n_arr = geo["n_ra"] + geo["n_va"]
+    zc_t = torch.empty((1 << geo["r"]) * n_arr * max(1 << c for c in geo["cbn"][:n_arr]), dtype=torch.int16,
+                       device=dev)
+    za_t = torch.empty(1 << geo["r"], n_arr, dtype=torch.int64, device=dev)
+    eps_t = torch.empty(1 << geo["r"], dtype=torch.float64, device=dev)
+    zmax_t = torch.empty(1 << geo["r"], dtype=torch.int64, device=dev)
+    zc_ms = []
+    for rep in range(11):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = C.lib().cbaa_column_stats(cube.handle, theta, zc_t.data_ptr(), za_t.data_ptr(), eps_t.data_ptr(),
+                                       zmax_t.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        assert st == 0, st
+        torch.cuda.synchronize()
+        if rep:
+            zc_ms.append(e0.elapsed_time(e1))
+
     # timed region: double-buffered windows
     for k in range(max(args.warmup, 0)):
         piped_step(k)
@@ -529,6 +558,16 @@ def run_cbaa(args):
                    "steps": n_serial, "note": "one window at a time on one stream (reset, update, detect)"},
         "update_ms": statistics.mean(upd_ms), "update_gpps": n / upd_s / 1e9,
         "detect_ms": statistics.mean(det_ms), "detect_ms_p50": statistics.median(det_ms),
+        "detect_sync_ms": {"p50": statistics.median(det_sync_ms), "max": max(det_sync_ms),
+                           "what": "window close -> sorted host list in host memory (cbaa_detect, synchronous, "
+                                   "through the Python binding)"},
+        "detect_roofline": {"bound": "hbm", "kernel": "zero counts, eps and Zmax (cbaa_column_stats: memset, "
+                                                      "k_zero_counts, k_eps_zmax)",
+                            "achieved": cube.nbytes / (statistics.median(zc_ms) * 1e-3) / 1e9, "peak": hbm_peak,
+                            "unit": "GB/s",
+                            "frac": cube.nbytes / (statistics.median(zc_ms) * 1e-3) / 1e9 / hbm_peak,
+                            "ms": statistics.median(zc_ms),
+                            "note": "reads the cube once (M bytes); the cube is L2-resident after its update"},
         "hosts_detected": int(inf["n_hosts"]), "hot_columns": int(inf["n_hot"]),
         "update_path": path,
         "autotune": None if tuned is None else {
