@@ -877,11 +877,14 @@ def run_batched(args):
     assert np.array_equal(hosts_last, res[-1][0]), "plain and batched host lists differ"
     plain_value = total_packets * steps / (plain_ms * 1e-3) / 1e9
 
-    # the OR merge of Section III.C alone (a6): the 8 router cubes of the last window into a global cube;
-    # algorithmic bytes = every router cube read + the global cube read and written
+    # the OR merge of Section III.C alone (a6): the 8 router cubes of the last window into a global cube,
+    # as the graph does it (global = OR of the routers: every router cube read, the global cube written);
+    # beside it the merge into a global cube that keeps its bits (dst |= ..., dst read as well)
     merge_reps = 20
-    merge_ms = timed(lambda: rw.globs[0].merge(rw.routers), merge_reps) / merge_reps
-    merge_bytes = (R + 2) * C.cube_bytes(geo)
+    merge_ms = timed(lambda: rw.globs[0].merge(rw.routers, assign=True), merge_reps) / merge_reps
+    merge_bytes = (R + 1) * C.cube_bytes(geo)
+    merge_or_ms = timed(lambda: rw.globs[0].merge(rw.routers), merge_reps) / merge_reps
+    merge_or_bytes = (R + 2) * C.cube_bytes(geo)
     hbm_peak, hbm_src = measured_peaks()
     merge_gbs = merge_bytes / (merge_ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": steps,
@@ -892,16 +895,18 @@ def run_batched(args):
                        "router_loads": "lognormal(sigma=0.8) weights over a 5-tuple hash",
                        "geometry": "r=5, |RA|=3, |VA|=1, g=2^10, c=2^12 (64 MiB per cube)", "theta": theta,
                        "step": "one CUDA graph replay: per window reset router cubes, one partitioned update "
-                               "pass over all routers, OR-merge into global cube w mod 2, detect on a side "
-                               "stream (overlapping the next window's router update)",
+                               "pass over all routers, global cube w mod 2 = OR of the router cubes, detect on a "
+                               "side stream (overlapping the next window's router update)",
                        "l2": "inputs larger than L2 (2 GiB of packets per step)"},
             "window_ms": ms / steps / len(wins), "router_update_tiling": tiling,
             "plain_single_cube": {"value": plain_value, "unit": "Gpps", "window_ms": plain_ms / steps / len(wins),
                                   "path": "one cube, partitioned update of the whole window, detect, no graph"},
-            "merge": {"ms": merge_ms, "sources": R, "bytes": merge_bytes,
+            "merge": {"ms": merge_ms, "sources": R, "bytes": merge_bytes, "call": "cbaa_cube_merge_assign",
                       "roofline": {"bound": "hbm", "kernel": "k_merge", "achieved": merge_gbs, "peak": hbm_peak,
                                    "unit": "GB/s", "frac": merge_gbs / hbm_peak,
-                                   "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}},
+                                   "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"},
+                      "or_into": {"call": "cbaa_cube_merge", "ms": merge_or_ms, "bytes": merge_or_bytes,
+                                  "frac": merge_or_bytes / (merge_or_ms * 1e-3) / 1e9 / hbm_peak}},
             "hosts_per_window": [int(i["n_hosts"]) for _, i in res],
             "gpu_launches": steps * len(wins) * (update_kernels(True, C.get_tuning(), sum(n_per) // len(wins)) + 1 +
                                                  detect_kernels(geo)),

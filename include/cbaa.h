@@ -231,6 +231,13 @@ int cbaa_get_tuning(cbaa_tuning *t);
  * no-op; dst may not be among srcs. */
 int cbaa_cube_merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream);
 
+/* Section III.C merge into a fresh global cube, async: dst = src_0 | ... |
+ * src_{k-1} word by word -- the merge with an all-zero initial value --
+ * without reading dst, so no reset of dst is needed first (k = 0 zeroes
+ * dst).  Same checks and errors as cbaa_cube_merge; all sources are checked
+ * before anything is enqueued. */
+int cbaa_cube_merge_assign(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream);
+
 /* Column statistics of the end-of-window pass, async (Eq. 1, Thm. 1 and the
  * hot-column bound of Section III.C):
  *   dev_zc   uint16[S][A][cmax]: zero bits of every column (cmax = max c_a;

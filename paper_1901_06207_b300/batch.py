@@ -46,7 +46,7 @@ class RouterWindows:
 
     def enqueue_window(self, w: int, router_pairs, done=None):
         """One window on the current stream: reset router cubes, one update pass over all of them,
-        reset and merge into global cube w mod 2; its detect goes to the side stream.  `done[b]` is
+        global cube w mod 2 = OR of the router cubes; its detect goes to the side stream.  `done[b]` is
         the event after the last detect of global cube b (reset waits for it)."""
         torch = C._torch()
         main = torch.cuda.current_stream()
@@ -56,8 +56,7 @@ class RouterWindows:
         C.update_multi(self.routers, router_pairs, self.uws)
         if done is not None and done[b] is not None:
             main.wait_event(done[b])
-        self.globs[b].reset()
-        self.globs[b].merge(self.routers)
+        self.globs[b].merge(self.routers, assign=True)      # global = OR of the router cubes
         merged = torch.cuda.Event()
         merged.record(main)
         self.side.wait_event(merged)

@@ -87,6 +87,7 @@ def _signatures():
         "cbaa_cube_set_inner_net": (ctypes.c_int, [vp, ctypes.POINTER(InnerNet)]),
         "cbaa_cube_update": (ctypes.c_int, [vp, vp, sz, vp]),
         "cbaa_cube_merge": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.c_int, vp]),
+        "cbaa_cube_merge_assign": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.c_int, vp]),
         "cbaa_column_stats": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp, vp, vp, vp]),
         "cbaa_detect_async": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, sz, vp, vp]),
         "cbaa_detect_range_async": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp, sz,
@@ -320,9 +321,11 @@ class Cube:
         _check(lib().cbaa_cube_update_binned(self.handle, ptr, n, ws.ptr, ws.nbytes, _stream_ptr(stream)),
                "cube_update_binned")
 
-    def merge(self, others, stream=None):
+    def merge(self, others, stream=None, assign: bool = False):
+        """self |= OR(others); assign=True: self = OR(others) without reading self (no reset needed)."""
         arr = (ctypes.c_void_p * max(1, len(others)))(*[o.handle.value for o in others])
-        _check(lib().cbaa_cube_merge(self.handle, arr, len(others), _stream_ptr(stream)), "cube_merge")
+        fn = lib().cbaa_cube_merge_assign if assign else lib().cbaa_cube_merge
+        _check(fn(self.handle, arr, len(others), _stream_ptr(stream)), "cube_merge_assign" if assign else "cube_merge")
 
     def column_stats(self, theta: int, stream=None) -> dict:
         torch = _torch()

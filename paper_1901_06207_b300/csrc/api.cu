@@ -281,22 +281,40 @@ int cbaa_get_tuning(cbaa_tuning *t) {
     return CBAA_OK;
 }
 
-int cbaa_cube_merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// cbaa_cube_merge (assign false) and cbaa_cube_merge_assign.
+int merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream, bool assign) {
     if (!dst || k < 0 || (k > 0 && !srcs)) return CBAA_ERR_INVALID_ARG;
-    if (k == 0) return CBAA_OK;
+    if (k == 0) return assign ? cuda_status(cudaMemsetAsync(dst->data, 0, dst->bytes, as_stream(stream))) : CBAA_OK;
+    for (int j = 0; j < k; ++j) {                 // every source checked before anything is enqueued
+        const cbaa_cube *s = srcs[j];
+        if (!s || s == dst) return CBAA_ERR_INVALID_ARG;
+        if (std::memcmp(&s->p, &dst->p, sizeof(cbaa_params)) != 0) return CBAA_ERR_GEOMETRY;
+    }
     const uint32_t *ptrs[64];
     for (int k0 = 0; k0 < k; k0 += 64) {
         const int kk = (k - k0) < 64 ? (k - k0) : 64;
-        for (int j = 0; j < kk; ++j) {
-            const cbaa_cube *s = srcs[k0 + j];
-            if (!s || s == dst) return CBAA_ERR_INVALID_ARG;
-            if (std::memcmp(&s->p, &dst->p, sizeof(cbaa_params)) != 0) return CBAA_ERR_GEOMETRY;
-            ptrs[j] = s->data;
-        }
-        const int st = cuda_status(cbaa::launch_merge(dst->data, ptrs, kk, dst->G.cube_words, as_stream(stream)));
+        for (int j = 0; j < kk; ++j) ptrs[j] = srcs[k0 + j]->data;
+        const int st = cuda_status(cbaa::launch_merge(dst->data, ptrs, kk, dst->G.cube_words, as_stream(stream),
+                                                      assign && k0 == 0));
         if (st != CBAA_OK) return st;
     }
     return CBAA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cbaa_cube_merge(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream) {
+    return merge(dst, srcs, k, stream, false);
+}
+
+int cbaa_cube_merge_assign(cbaa_cube *dst, const cbaa_cube *const *srcs, int k, void *stream) {
+    return merge(dst, srcs, k, stream, true);
 }
 
 int cbaa_column_stats(const cbaa_cube *cube, uint32_t theta, uint16_t *dev_zc, uint64_t *dev_za, double *dev_eps,

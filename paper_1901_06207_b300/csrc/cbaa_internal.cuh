@@ -136,7 +136,9 @@ int cuda_status(cudaError_t e);
 int num_sms();   // SM count of the current device (cached on first use)
 cudaError_t launch_update(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, uint32_t blocks_per_sm,
                           cudaStream_t s);
-cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint64_t words, cudaStream_t s);
+// dst |= OR(srcs); assign: dst = OR(srcs) (dst is not read).
+cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint64_t words, cudaStream_t s,
+                         bool assign = false);
 // Zero counts, ε and Zmax of the sketches [cs_lo, cs_hi) (cs_hi = 0: all).
 cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc, uint64_t *za,
                                 double *eps, int64_t *zmax, double E, cudaStream_t s, uint32_t cs_lo = 0,

@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(256) k_update(const Geo G, uint32_t *__restric
 }
 
 // ---------------------------------------------------------------------------
-// Merge: dst |= OR of up to kMaxSrc sources per launch, 128-bit words.
+// Merge: dst |= OR of up to kMaxSrc sources per launch, 128-bit words
+// (assign: dst = OR of the sources, dst not read).
 
 constexpr int kMaxSrc = 16;
 struct SrcList {
@@ -98,14 +99,14 @@ struct SrcList {
 
 // Every source's 16 bytes are loaded before the first OR, so a thread keeps
 // L.k + 1 loads in flight.
-__global__ void __launch_bounds__(256) k_merge(uint4 *__restrict__ dst, const SrcList L, uint64_t n16) {
+__global__ void __launch_bounds__(256) k_merge(uint4 *__restrict__ dst, const SrcList L, uint64_t n16, bool assign) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
         uint4 b[kMaxSrc];
 #pragma unroll
         for (int k = 0; k < kMaxSrc; ++k)
             if (k < L.k) b[k] = ld_stream(L.p[k] + i);
-        uint4 a = dst[i];
+        uint4 a = assign ? make_uint4(0u, 0u, 0u, 0u) : dst[i];
 #pragma unroll
         for (int k = 0; k < kMaxSrc; ++k)
             if (k < L.k) { a.x |= b[k].x; a.y |= b[k].y; a.z |= b[k].z; a.w |= b[k].w; }
@@ -265,7 +266,8 @@ cudaError_t launch_update(const Geo &G, uint32_t *cube, const uint32_t *pairs, s
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint64_t words, cudaStream_t s) {
+cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint64_t words, cudaStream_t s,
+                         bool assign) {
     const uint64_t n16 = words / 4;
     const uint64_t cap = (uint64_t)num_sms() * 8;
     uint64_t want = (n16 + 255) / 256;
@@ -274,7 +276,7 @@ cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint
         SrcList L;
         L.k = (k - k0) < kMaxSrc ? (k - k0) : kMaxSrc;
         for (int j = 0; j < L.k; ++j) L.p[j] = reinterpret_cast<const uint4 *>(srcs[k0 + j]);
-        k_merge<<<blocks, 256, 0, s>>>(reinterpret_cast<uint4 *>(dst), L, n16);
+        k_merge<<<blocks, 256, 0, s>>>(reinterpret_cast<uint4 *>(dst), L, n16, assign && k0 == 0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

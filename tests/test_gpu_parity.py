@@ -245,6 +245,31 @@ def test_merge_equals_union(C, oracle, k):
     assert np.array_equal(dst.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
+@pytest.mark.parametrize("k", [0, 1, 3, 20])
+def test_merge_assign_replaces_dst(C, oracle, k):
+    """cbaa_cube_merge_assign: a global cube full of an earlier window's bits becomes exactly the
+    OR of the router cubes, i.e. the cube of all their traffic (k = 0: an empty cube)."""
+    import torch
+    d = GEO.TINY2
+    w = window("tiny")
+    rid, _ = T.split_by_router(w.pairs, 78, max(k, 1))
+    routers = []
+    for i in range(k):
+        c = C.Cube(d)
+        c.update(dev_pairs(w.pairs[rid == i]))
+        routers.append(c)
+    dst = C.Cube(d)
+    dst.memory.copy_(torch.randint(-2**31, 2**31 - 1, dst.memory.shape, device="cuda", dtype=torch.int32))
+    dst.merge(routers, assign=True)
+    want = oracle.build_cube(d, w.pairs) if k else np.zeros_like(dst.to_numpy())
+    assert np.array_equal(dst.to_numpy(), want)
+    if k:
+        bad = C.Cube(GEO.TINY)
+        with pytest.raises(C.CbaaError):
+            dst.merge(routers + [bad], assign=True)      # checked before anything is enqueued
+        assert np.array_equal(dst.to_numpy(), want)
+
+
 def test_merge_geometry_mismatch(C):
     a, b = C.Cube(GEO.TINY), C.Cube(GEO.with_form(GEO.TINY, 1))
     with pytest.raises(C.CbaaError) as e:
