@@ -140,7 +140,8 @@ cudaError_t launch_update(const Geo &G, uint32_t *cube, const uint32_t *pairs, s
 cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint64_t words, cudaStream_t s,
                          bool assign = false);
 // Zero counts, ε and Zmax of the sketches [cs_lo, cs_hi) (cs_hi = 0: all).
+// za_zeroed: the caller has already zeroed za (else it is zeroed here).
 cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc, uint64_t *za,
                                 double *eps, int64_t *zmax, double E, cudaStream_t s, uint32_t cs_lo = 0,
-                                uint32_t cs_hi = 0, uint32_t *done = nullptr);
+                                uint32_t cs_hi = 0, uint32_t *done = nullptr, bool za_zeroed = false);
 }  // namespace cbaa

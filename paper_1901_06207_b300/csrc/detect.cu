@@ -397,9 +397,11 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
     WsPtrs P = ws_pointers(G, Ly, ws);
     const double E = std::exp(-((double)theta / (double)G.g));
 
-    cudaError_t e = cudaMemsetAsync(P.state, 0, sizeof(DevState), s);
+    // the state words and the array zero totals (laid out next to each other) in one memset
+    const size_t cleared = Ly.za - Ly.state + sizeof(uint64_t) * (size_t)(G.smask + 1) * G.A;
+    cudaError_t e = cudaMemsetAsync(P.state, 0, cleared, s);
     if (e != cudaSuccess) return cuda_status(e);
-    e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s, cs_lo, cs_hi, &P.state->stats_done);
+    e = launch_column_stats(G, cube, P.zc, P.za, P.eps, P.zmax, E, s, cs_lo, cs_hi, &P.state->stats_done, true);
     if (e != cudaSuccess) return cuda_status(e);
     k_hot_lists<<<dim3(cs_hi - cs_lo, G.n_ra), 1024, 0, s>>>(G, P, cs_lo);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);

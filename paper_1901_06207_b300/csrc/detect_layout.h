@@ -63,8 +63,8 @@ inline WsLayout ws_layout(const Geo &G, uint64_t m) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
     L.state = take(sizeof(DevState));
+    L.za = take(sizeof(uint64_t) * S * G.A);          // right after the state: one memset clears both
     L.zc = take(sizeof(uint16_t) * S * G.A * G.cmax);
-    L.za = take(sizeof(uint64_t) * S * G.A);
     L.eps = take(sizeof(double) * S);
     L.zmax = take(sizeof(int64_t) * S);
     L.hc = take(sizeof(uint16_t) * S * G.n_ra * L.hc_stride);

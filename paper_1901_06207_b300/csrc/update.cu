@@ -285,10 +285,11 @@ cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint
 
 cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc, uint64_t *za,
                                 double *eps, int64_t *zmax, double E, cudaStream_t s, uint32_t cs_lo,
-                                uint32_t cs_hi, uint32_t *done) {
+                                uint32_t cs_hi, uint32_t *done, bool za_zeroed) {
     if (cs_hi == 0) cs_hi = G.smask + 1;
-    cudaError_t e = cudaMemsetAsync(za, 0, sizeof(uint64_t) * (size_t)(G.smask + 1) * G.A, s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!za_zeroed && (e = cudaMemsetAsync(za, 0, sizeof(uint64_t) * (size_t)(G.smask + 1) * G.A, s)) != cudaSuccess)
+        return e;
     if (cs_lo >= cs_hi) return cudaSuccess;
     const uint32_t arrays = (cs_hi - cs_lo) * G.A;
     // Enough blocks to cover every SM several times; each slice is whole columns.
