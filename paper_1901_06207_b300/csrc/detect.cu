@@ -328,8 +328,9 @@ __device__ void bitonic_out(WsPtrs P, uint32_t n, cbaa_host *__restrict__ out, u
     for (uint32_t k = threadIdx.x; k < nw; k += blockDim.x) out[k] = P.hosts[keys[k] & 0xFFFFFFFFull];
 }
 
+// info_copy (may be null): where the settled detect info is also written.
 __global__ void __launch_bounds__(kRankThreads) k_sort(const Geo G, WsPtrs P, cbaa_host *__restrict__ out,
-                                                       uint64_t cap) {
+                                                       uint64_t cap, cbaa_detect_info *__restrict__ info_copy) {
     __shared__ uint32_t keys[kRankTile];
     __shared__ unsigned long long skeys[kSmemKeys];
     DevState *st = P.state;
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(kRankThreads) k_sort(const Geo G, WsPtrs P, cb
         st->info.n_tuples = tuples;
         st->info.need_tuples = need;
         st->info.status = need ? CBAA_ERR_WORKSPACE : (found > cap ? CBAA_ERR_CAPACITY : CBAA_OK);
+        if (info_copy) *info_copy = st->info;        // every other field was final before this kernel
     }
     if (n > kRankMax) {
         if (blockIdx.x == 0) bitonic_out(P, n, out, cap, skeys);
@@ -423,12 +425,8 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
     const uint64_t rank_n = P.m < kRankMax ? P.m : kRankMax;
     const uint64_t per_block = kRankThreads / kRankLanes;
     const uint64_t sort_blocks = (rank_n + per_block - 1) / per_block;
-    k_sort<<<(unsigned)(sort_blocks ? sort_blocks : 1), kRankThreads, 0, s>>>(G, P, dst, dcap);
+    k_sort<<<(unsigned)(sort_blocks ? sort_blocks : 1), kRankThreads, 0, s>>>(G, P, dst, dcap, info_copy);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    if (info_copy) {
-        e = cudaMemcpyAsync(info_copy, &P.state->info, sizeof(cbaa_detect_info), cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
     return CBAA_OK;
 }
 
