@@ -494,15 +494,37 @@ struct Overflow {
     uint32_t cap;
 };
 
+// Tile tables of a routing block in a pass over several cubes.  A block
+// numbers only the tiles of the router segments its packets meet
+// (BlockTiles), so its shared-memory tables need span x tiles-per-cube
+// entries, span the most segments any block of P packets meets -- one,
+// unless a segment starts inside the block's range -- and never more than
+// the pass's nb tiles.  Sizing the tables for that instead of nb lets more
+// blocks share an SM.
+uint32_t routing_table_tiles(const Geo &G, const BinSegs &S, uint32_t nb, uint64_t P) {
+    const uint64_t tpr = (uint64_t)(G.smask + 1) * G.W;
+    uint64_t span_max = 1;
+    for (uint32_t j = 1; j < S.k; ++j) {              // the block holding segment j's first packet
+        const uint64_t lo = S.start[j] / P * P, hi = lo + P;
+        uint64_t span = 0;
+        for (uint32_t t = 0; t < S.k; ++t)
+            if (S.start[t] < hi && S.start[t + 1] > lo) ++span;
+        if (span > span_max) span_max = span;
+    }
+    return span_max * tpr < nb ? (uint32_t)(span_max * tpr) : nb;
+}
+
 template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT>
 cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                               const Overflow &O, cudaStream_t s) {
+    // several cubes: every block numbers its own tiles within tables of nbt entries
+    const uint32_t nbt = MULTI ? routing_table_tiles(G, S, nb, (uint64_t)THREADS * PPT) : nb;
     const size_t per = SHORT ? 2 : 3;                 // staged record words + bin word per packet
-    const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nb + 1) & ~(size_t)1) + per * THREADS * PPT);
+    const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nbt + 1) & ~(size_t)1) + per * THREADS * PPT);
     cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT>, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
-    k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT><<<blocks, THREADS, smem, s>>>(G, S, m, nb, W.cursors, W.codes,
+    k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT><<<blocks, THREADS, smem, s>>>(G, S, m, nbt, W.cursors, W.codes,
                                                                                 W.offsets, O.list, O.count, O.cap);
     return cudaGetLastError();
 }
@@ -520,7 +542,8 @@ cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, 
         case 7: return launch_rt_scatter<256, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
         case 8: {
             // 1024 x 16 stages 16Ki records: with 8-byte records or many tiles it exceeds shared memory
-            const size_t need = sizeof(uint32_t) * ((((size_t)3 * nb + 1) & ~(size_t)1) + (SHORT ? 2 : 3) * 16384);
+            const uint32_t nbt = MULTI ? routing_table_tiles(G, S, nb, 16384) : nb;
+            const size_t need = sizeof(uint32_t) * ((((size_t)3 * nbt + 1) & ~(size_t)1) + (SHORT ? 2 : 3) * 16384);
             if (need + 1024 > 227u * 1024u) return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
             return launch_rt_scatter<1024, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
         }
