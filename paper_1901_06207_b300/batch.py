@@ -79,7 +79,8 @@ class RouterWindows:
         main.wait_stream(self.side)
 
     def tune(self, windows, reps: int = 3):
-        """Pick the tiling of the partitioned update for these router cubes by timing the first window.
+        """Pick the tiling and routing shape of the partitioned update for these router cubes by
+        timing the first window (tile kinds 1-3 x routing shapes of 8 and 16 packets per thread).
 
         Sets the process-wide tuning; call before capture() so the graph records the choice."""
         torch = C._torch()
@@ -87,23 +88,24 @@ class RouterWindows:
         best = None
         base = C.get_tuning()
         for kind in (1, 2, 3):
-            C.set_tuning(**{**base, "tile_kind": kind})
-            times = []
-            for rep in range(reps + 1):
-                for c in self.routers:
-                    c.reset()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                C.update_multi(self.routers, windows[0], self.uws)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                if rep:
-                    times.append(e0.elapsed_time(e1))
-            t = sorted(times)[len(times) // 2]
-            if best is None or t < best[1]:
-                best = (kind, t)
-        C.set_tuning(**{**base, "tile_kind": best[0]})
-        return {"tile_kind": best[0], "update_ms": best[1]}
+            for shape in ((0,) if kind == 1 else (0, 6, 8)):      # column tiles take one shape
+                C.set_tuning(**{**base, "tile_kind": kind, "scatter_shape": shape})
+                times = []
+                for rep in range(reps + 1):
+                    for c in self.routers:
+                        c.reset()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    C.update_multi(self.routers, windows[0], self.uws)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if rep:
+                        times.append(e0.elapsed_time(e1))
+                t = sorted(times)[len(times) // 2]
+                if best is None or t < best[2]:
+                    best = (kind, shape, t)
+        C.set_tuning(**{**base, "tile_kind": best[0], "scatter_shape": best[1]})
+        return {"tile_kind": best[0], "scatter_shape": best[1], "update_ms": best[2]}
 
     def capture(self, windows):
         """Record every window into one CUDA graph (after one eager pass on a side stream)."""
