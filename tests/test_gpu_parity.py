@@ -150,6 +150,31 @@ def _multi_router_case(C, oracle, geo, win, k):
     assert np.array_equal(glob.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
+@pytest.mark.parametrize("shape", [0, 6])
+@pytest.mark.parametrize("kind", [2, 3])
+def test_multi_router_segment_edges(C, oracle, shape, kind):
+    """Router segments of 0, 1, 2 and about one routing block of packets (4096 or 8192): some
+    blocks meet many segments, so the routing tables fall back to every cube's tiles, others meet
+    one or two; every cube must still be the oracle's cube of its own packets."""
+    d = GEO.TINY
+    rng = np.random.default_rng(41)
+    P = 4096 if shape == 0 else 8192
+    lens = [1, 0, 2, 3, P - 1, 1, 1, P, P + 1, 2 * P + 5, 7, 5 * P, 1, 0, 3 * P - 2, 1]
+    pairs = rng.integers(0, 2**32, size=(sum(lens), 2), dtype=np.uint64).astype(np.uint32)
+    cut = np.concatenate([[0], np.cumsum(lens)])
+    parts = [pairs[cut[j]:cut[j + 1]] for j in range(len(lens))]
+    before = C.get_tuning()
+    try:
+        C.set_tuning(**{**before, "tile_kind": kind, "scatter_shape": shape})
+        cubes = [C.Cube(d) for _ in parts]
+        C.update_multi(cubes, [dev_pairs(p) if p.shape[0] else None for p in parts],
+                       C.UpdateWorkspace(d, pairs.shape[0], n_cubes=len(parts)))
+        for j, p in enumerate(parts):
+            assert np.array_equal(cubes[j].to_numpy(), oracle.build_cube(d, p)), j
+    finally:
+        C.set_tuning(**before)
+
+
 @pytest.mark.parametrize("kind", [1, 2, 3])
 @pytest.mark.parametrize("geo", ["L2", "PAPER"])
 def test_binned_update_skewed_runs(C, oracle, geo, kind):
