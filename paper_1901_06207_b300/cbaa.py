@@ -289,6 +289,15 @@ class Cube:
         torch.cuda.synchronize()
         return self.memory.view(torch.int32).cpu().numpy().view(np.uint32)
 
+    def load_numpy(self, words: np.ndarray):
+        """Restore cube words taken by to_numpy() (a checkpoint of a window in progress) into this
+        cube, which must have the snapshot's geometry; later updates OR into the restored bits."""
+        torch = _torch()
+        w = np.ascontiguousarray(words, dtype=np.uint32).reshape(-1)
+        if w.size * 4 != self.nbytes:
+            raise CbaaError(ERR_INVALID_ARG, f"snapshot of {w.size * 4} bytes for a {self.nbytes}-byte cube")
+        self.memory.view(torch.int32)[: w.size].copy_(torch.from_numpy(w.view(np.int32)))
+
     def reset(self, stream=None):
         _check(lib().cbaa_cube_reset(self.handle, _stream_ptr(stream)), "cube_reset")
 

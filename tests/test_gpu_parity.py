@@ -244,6 +244,28 @@ def test_update_ragged_and_unaligned(C, oracle):
     assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
+def test_checkpoint_and_resume(C, oracle):
+    """A window checkpointed mid-way (cube words to the host), restored into a fresh cube and
+    finished there equals the window run without interruption, and the oracle."""
+    d = GEO.L2
+    w = window("4m")
+    p = dev_pairs(w.pairs)
+    half = 1_234_567
+    ws = C.UpdateWorkspace(d, w.pairs.shape[0])
+    a = C.Cube(d)
+    a.update_binned(p[:half], ws)
+    snap = a.to_numpy().copy()
+    b = C.Cube(d)
+    b.load_numpy(snap)
+    b.update_binned(p[half:], ws)
+    whole = C.Cube(d)
+    whole.update_binned(p, ws)
+    assert np.array_equal(b.to_numpy(), whole.to_numpy())
+    assert np.array_equal(b.to_numpy(), oracle.build_cube(d, w.pairs))
+    with pytest.raises(C.CbaaError):
+        C.Cube(GEO.TINY).load_numpy(snap)
+
+
 def test_update_order_and_duplicates(C):
     d = GEO.TINY
     w = window("tiny")

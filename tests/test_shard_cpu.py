@@ -83,3 +83,42 @@ def test_owned_ranges_partition_the_sketches():
         assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
     with pytest.raises(ValueError):
         shard.owned_range(geo, 0, 3)
+
+
+def _fail_main(rank, world, port, mode, out):
+    """Rank 1 fails before the sketch exchange (exits, or stalls past the group's timeout); rank 0
+    must come back from the exchange with an error instead of waiting forever."""
+    import datetime
+    import sys
+    import time
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+    import torch.distributed as dist
+    from paper_1901_06207_b300 import shard
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=3))
+    if rank == 1:
+        if mode == "exit":
+            os._exit(0)                                    # gone mid-window, no goodbye
+        time.sleep(8)                                      # alive, but never joins the exchange
+        os._exit(0)
+    mem = torch.from_numpy(_words(rank, 1024).view(np.int32).copy())
+    recv = torch.empty_like(mem)
+    t0 = time.perf_counter()
+    try:
+        shard.exchange_slices(mem, rank, world, recv, lambda d, srcs: None)
+        out[0] = ("no error", time.perf_counter() - t0)
+    except Exception as e:  # noqa: BLE001 -- any collective error is the detection
+        out[0] = (type(e).__name__, time.perf_counter() - t0)
+    os._exit(0)
+
+
+@pytest.mark.parametrize("mode", ["exit", "stall"])
+def test_failed_rank_is_detected_on_the_host(mode):
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_fail_main, args=(2, port, mode, out), nprocs=2, join=True)
+    what, waited = out[0]
+    assert what != "no error", what
+    assert waited < 10.0, waited
