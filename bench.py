@@ -981,6 +981,19 @@ def run_serve(args):
     pk_p = sum(r.packets for r in res_p)
     pk_c = sum(r.packets for r in res_c)
     cap_gpps = reduce_over_ranks(pk_c, world, "sum", dev) / reduce_over_ranks(el_c, world, "max", dev) / 1e9
+    # the capacity's bound on this host: a plain pinned host-to-device copy of a slot's worth of pairs
+    dst = torch.empty((4 << 20, 2), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h2d = []
+    for rep in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dst.copy_(pool[:4 << 20], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            h2d.append(dst.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    h2d_gbs = max(h2d)
     line = {"metric": METRIC, "value": cap_gpps, "unit": "Gpps", "n_gpus": world, "steps": len(res_c),
             "warmup": 1, "ms_per_step": 1e3 * el_c / max(1, len(res_c)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -994,7 +1007,11 @@ def run_serve(args):
                       "latency_ms_p50": lat[len(lat) // 2] if lat else None,
                       "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
                       "latency": "window close -> host list on the host"},
-            "capacity": {"packets": pk_c, "seconds": el_c, "windows": len(res_c)},
+            "capacity": {"packets": pk_c, "seconds": el_c, "windows": len(res_c),
+                         "roofline": {"bound": "h2d", "achieved": 8 * pk_c / el_c / 1e9, "peak": h2d_gbs,
+                                      "unit": "GB/s", "frac": 8 * pk_c / el_c / 1e9 / h2d_gbs,
+                                      "peak_source": "pinned host-to-device copy of 4Mi pairs alone, "
+                                                     "measured in this run"}},
             "server_stats": dict(srv.stats),
             "hosts_per_window": [int(r.info["n_hosts"]) for r in res_p],
             "clocks": clocks.summary()}
