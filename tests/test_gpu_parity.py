@@ -244,6 +244,26 @@ def test_update_ragged_and_unaligned(C, oracle):
     assert np.array_equal(cube.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
+@pytest.mark.parametrize("kind", [2, 3])
+@pytest.mark.parametrize("r,cbn", [(8, 12), (7, 13)])
+def test_largest_row_tile_geometry(C, oracle, kind, r, cbn):
+    """512 MiB cubes, the most the partitioned update takes: r=8, c=2^12 has the most row tiles
+    (8192 of 64 KiB), r=7, c=2^13 the largest ones (4096 of 128 KiB).  Cube bit-exact and host
+    list equal to the oracle's."""
+    d = C.make_params(r, 3, 1, 10, [cbn])
+    w = window("4m")
+    before = C.get_tuning()
+    try:
+        C.set_tuning(**{**before, "tile_kind": kind})
+        cube = C.Cube(d)
+        cube.update_binned(dev_pairs(w.pairs), C.UpdateWorkspace(d, w.pairs.shape[0]))
+        want_cube = oracle.build_cube(d, w.pairs)
+        assert np.array_equal(cube.to_numpy(), want_cube)
+        assert_hosts_equal(cube.detect(1024), oracle.detect(d, want_cube, 1024)["hosts"])
+    finally:
+        C.set_tuning(**before)
+
+
 def test_checkpoint_and_resume(C, oracle):
     """A window checkpointed mid-way (cube words to the host), restored into a fresh cube and
     finished there equals the window run without interruption, and the oracle."""
