@@ -374,7 +374,10 @@ DETECT_CASES = [("TINY", "tiny", 128, 0), ("TINY", "tiny", 96, 1), ("TINY", "tin
                 ("TINY2", "tiny", 128, 0), ("PAPER", "1m", 1024, 0), ("PAPER", "1m", 1024, 1),
                 ("L2", "4m", 1024, 0), ("L2", "4m", 700, 1), ("UNDERSIZED", "4m", 1024, 0),
                 ("SERVE", "4m", 1024, 0), ("QUAD", "tiny", 128, 0),
-                ("DUO", "tiny", 128, 1)]
+                ("DUO", "tiny", 128, 1),
+                # theta beyond any estimate: form 0 keeps Zmax = 0 (only saturated columns are hot,
+                # every host has Z = 0), form 1 makes it negative (no hot column, no host)
+                ("TINY", "tiny_sat", 1 << 20, 0), ("TINY", "tiny_sat", 1 << 20, 1)]
 
 
 @pytest.mark.parametrize("geo,win,theta,form", DETECT_CASES)
@@ -387,8 +390,11 @@ def test_detect_host_list_parity(C, oracle, geo, win, theta, form):
     want = oracle.detect(d, oracle.build_cube(d, w.pairs), theta)["hosts"]
     assert_hosts_equal(got, want)
     assert np.all(np.diff(got["ip"].astype(np.int64)) > 0)       # sorted, no duplicates
-    if win == "tiny_sat":
+    if win == "tiny_sat" and theta < (1 << 20):
         assert (got["flags"] & C.FLAG_SATURATED).any()
+    if theta >= (1 << 20):
+        assert np.all(got["z"] == 0) and np.all(got["flags"] & C.FLAG_SATURATED)
+        assert (got.size > 0) == (form == 0), got.size
 
 
 def test_detect_empty_cube_and_repeat(C):
