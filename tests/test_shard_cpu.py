@@ -95,17 +95,23 @@ def _fail_main(rank, world, port, mode, out):
     import torch
     import torch.distributed as dist
     from paper_1901_06207_b300 import shard
-    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
-                            timeout=datetime.timedelta(seconds=3))
+    def group():
+        dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                                timeout=datetime.timedelta(seconds=3))
+
     if rank == 1:
-        if mode == "exit":
-            os._exit(0)                                    # gone mid-window, no goodbye
-        time.sleep(8)                                      # alive, but never joins the exchange
-        os._exit(0)
-    mem = torch.from_numpy(_words(rank, 1024).view(np.int32).copy())
-    recv = torch.empty_like(mem)
+        try:
+            group()
+        except Exception:  # noqa: BLE001 -- the failing rank's own errors do not matter
+            pass
+        if mode == "stall":
+            time.sleep(8)                                  # alive, but never joins the exchange
+        os._exit(0)                                        # gone mid-window, no goodbye
     t0 = time.perf_counter()
-    try:
+    try:                                                   # rank 1 may already be gone during the setup
+        group()
+        mem = torch.from_numpy(_words(rank, 1024).view(np.int32).copy())
+        recv = torch.empty_like(mem)
         shard.exchange_slices(mem, rank, world, recv, lambda d, srcs: None)
         out[0] = ("no error", time.perf_counter() - t0)
     except Exception as e:  # noqa: BLE001 -- any collective error is the detection
