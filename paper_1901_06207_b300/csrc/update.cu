@@ -8,6 +8,8 @@
 // is read with 128-bit loads marked evict-first so that it does not push
 // the cube out of L2; the cube itself is left with the default policy and
 // stays L2-resident when it fits.
+#include <atomic>
+
 #include "cbaa_internal.cuh"
 
 namespace cbaa {
@@ -237,16 +239,20 @@ __global__ void k_eps_zmax(const Geo G, const unsigned long long *__restrict__ z
 
 }  // namespace
 
-static int g_num_sms = 0;
+// SM count of the first device asked (only grid sizes depend on it); host
+// threads may race to fill it in, with the same value.
+static std::atomic<int> g_num_sms{0};
 
 int num_sms() {
-    if (g_num_sms == 0) {
+    int n = g_num_sms.load(std::memory_order_relaxed);
+    if (n == 0) {
         int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 148;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 148;
+        g_num_sms.store(n, std::memory_order_relaxed);
     }
-    return g_num_sms;
+    return n;
 }
 
 // ---------------------------------------------------------------------------
