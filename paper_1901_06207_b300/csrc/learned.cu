@@ -138,28 +138,37 @@ __global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16 *__rest
 }
 
 // Gradient of sum_s (y_s - t_s)^2 * scale over all n samples, accumulated into
-// grad (FP32, parameter layout) and loss_sum.  Persistent blocks of TB
-// threads walk tiles of TB samples; activations and deltas of a tile live in
-// shared memory as [feature][sample] rows padded to TB+1 floats, so both the
-// per-sample passes and the per-weight reductions are free of bank
-// conflicts.  Each block keeps its weight gradients in registers over all
-// its tiles and adds them to `grad` once at the end.
+// grad (FP32, parameter layout) and loss_sum.  Blocks of TB threads walk
+// tiles of TILE samples: the PARTS threads of a sample each take HID/PARTS
+// hidden units through the forward and backward passes, with activations
+// and deltas in shared memory as [feature][sample] rows padded to TILE+1
+// floats (conflict-free in both the per-sample passes and the per-weight
+// reductions); then every thread accumulates its share of the weight
+// gradients over the tile's samples in registers, and adds them to `grad`
+// once at the end.  Small tiles spread a batch over many SMs (a 4096-sample
+// batch fills 128 blocks).
 constexpr int TB = 128;
-constexpr int LD = TB + 1;
+constexpr int TILE = 32;
+constexpr int PARTS = TB / TILE;
+constexpr int HP = HID / PARTS;
+constexpr int LD = TILE + 1;
+static_assert(TB % TILE == 0 && HID % PARTS == 0, "tile split");
 
 __global__ void __launch_bounds__(TB) k_mlp_grad(const __nv_bfloat16 *__restrict__ Wb, const float *__restrict__ X,
                                                  const float *__restrict__ Tgt, uint64_t n, float scale,
                                                  float *__restrict__ grad, float *__restrict__ loss_sum) {
     extern __shared__ float sm[];
     float *w = sm;                         // NPAR
-    float *Xs = w + ((NPAR + 3) & ~3);     // IN x LD
-    float *H1 = Xs + IN * LD;              // HID x LD
+    float *H1 = w + ((NPAR + 3) & ~3);     // HID x LD
     float *H2 = H1 + HID * LD;
     float *D1 = H2 + HID * LD;
     float *D2 = D1 + HID * LD;
-    float *D3 = D2 + HID * LD;             // LD
+    float *Xs = D2 + HID * LD;             // IN x LD
+    float *Yp = Xs + IN * LD;              // PARTS x LD: each part's share of the output
+    float *D3 = Yp + PARTS * LD;           // LD
     load_weights(Wb, w);
     const int k = threadIdx.x;
+    const int sl = k % TILE, i0 = (k / TILE) * HP;   // this thread's sample in the tile, first hidden unit
     // register accumulators: W2 rows ib2*32.. of column j2, W1 rows ib1*8.. of column j1
     const int j2 = k & 63, ib2 = k >> 6, j1 = k & 15, ib1 = k >> 4;
     float g2[32], g1[8];
@@ -169,9 +178,9 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(const __nv_bfloat16 *__restrict
     for (int q = 0; q < 8; ++q) g1[q] = 0.f;
     float gw3 = 0.f, gb2 = 0.f, gb1 = 0.f, gb3 = 0.f, lsum = 0.f;
     __syncthreads();
-    const uint64_t tiles = (n + TB - 1) / TB;
+    const uint64_t tiles = (n + TILE - 1) / TILE;
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const uint64_t s = tile * TB + k;
+        const uint64_t s = tile * TILE + sl;
         const bool valid = s < n;
         float x[IN];
         if (valid) {
@@ -180,34 +189,45 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(const __nv_bfloat16 *__restrict
 #pragma unroll
             for (int j = 0; j < IN; ++j) x[j] = 0.f;
         }
+        if (i0 == 0) {
 #pragma unroll
-        for (int j = 0; j < IN; ++j) Xs[j * LD + k] = x[j];
-        for (int i = 0; i < HID; ++i) {
+            for (int j = 0; j < IN; ++j) Xs[j * LD + sl] = x[j];
+        }
+        for (int i = i0; i < i0 + HP; ++i) {
             float a = w[OB1 + i];
 #pragma unroll
             for (int j = 0; j < IN; ++j) a = fmaf(w[OW1 + i * IN + j], x[j], a);
-            H1[i * LD + k] = fmaxf(a, 0.f);
+            H1[i * LD + sl] = fmaxf(a, 0.f);
         }
-        float y = w[OB3];
-        for (int i = 0; i < HID; ++i) {
+        __syncthreads();                                   // H1 of the tile complete
+        float yp = 0.f;
+        for (int i = i0; i < i0 + HP; ++i) {
             float a = w[OB2 + i];
-            for (int j = 0; j < HID; ++j) a = fmaf(w[OW2 + i * HID + j], H1[j * LD + k], a);
+            for (int j = 0; j < HID; ++j) a = fmaf(w[OW2 + i * HID + j], H1[j * LD + sl], a);
             const float h = fmaxf(a, 0.f);
-            H2[i * LD + k] = h;
-            y = fmaf(w[OW3 + i], h, y);
+            H2[i * LD + sl] = h;
+            yp = fmaf(w[OW3 + i], h, yp);
         }
+        Yp[(i0 / HP) * LD + sl] = yp;
+        __syncthreads();                                   // every part's share of y complete
+        float y = w[OB3];
+#pragma unroll
+        for (int p = 0; p < PARTS; ++p) y += Yp[p * LD + sl];
         const float r = valid ? (y - Tgt[s]) : 0.f;
-        lsum = fmaf(r, r, lsum);
         const float d3 = 2.f * r * scale;
-        D3[k] = d3;
-        for (int i = 0; i < HID; ++i) D2[i * LD + k] = (H2[i * LD + k] > 0.f) ? d3 * w[OW3 + i] : 0.f;
-        for (int j = 0; j < HID; ++j) {
-            float a = 0.f;
-            for (int i = 0; i < HID; ++i) a = fmaf(D2[i * LD + k], w[OW2 + i * HID + j], a);
-            D1[j * LD + k] = (H1[j * LD + k] > 0.f) ? a : 0.f;
+        if (i0 == 0) {
+            lsum = fmaf(r, r, lsum);
+            D3[sl] = d3;
         }
-        __syncthreads();
-        for (int t = 0; t < TB; ++t) {
+        for (int i = i0; i < i0 + HP; ++i) D2[i * LD + sl] = (H2[i * LD + sl] > 0.f) ? d3 * w[OW3 + i] : 0.f;
+        __syncthreads();                                   // D2 complete
+        for (int j = i0; j < i0 + HP; ++j) {
+            float a = 0.f;
+            for (int i = 0; i < HID; ++i) a = fmaf(D2[i * LD + sl], w[OW2 + i * HID + j], a);
+            D1[j * LD + sl] = (H1[j * LD + sl] > 0.f) ? a : 0.f;
+        }
+        __syncthreads();                                   // D1, D3 and Xs complete
+        for (int t = 0; t < TILE; ++t) {
             const float h1 = H1[j2 * LD + t];
 #pragma unroll
             for (int q = 0; q < 32; ++q) g2[q] = fmaf(D2[(ib2 * 32 + q) * LD + t], h1, g2[q]);
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(const __nv_bfloat16 *__restrict
         atomicAdd(&grad[OB3], gb3);
     }
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if ((k & 31) == 0) atomicAdd(loss_sum, lsum);
+    if ((k & 31) == 0 && lsum != 0.f) atomicAdd(loss_sum, lsum);
 }
 
 // Adam on FP32 master weights; the BF16 copy the kernels read is rounded
@@ -299,7 +319,7 @@ cudaError_t launch_mlp_forward(const uint16_t *Wb, const float *X, uint64_t n, f
 }
 
 size_t mlp_grad_smem() {
-    return sizeof(float) * ((size_t)((NPAR + 3) & ~3) + (size_t)(IN + 4 * HID + 1) * LD);
+    return sizeof(float) * ((size_t)((NPAR + 3) & ~3) + (size_t)(4 * HID + IN + PARTS + 1) * LD);
 }
 
 cudaError_t launch_mlp_grad(const uint16_t *Wb, const float *X, const float *T, uint64_t n, float scale,
@@ -308,7 +328,7 @@ cudaError_t launch_mlp_grad(const uint16_t *Wb, const float *X, const float *T, 
     const size_t smem = mlp_grad_smem();
     cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const uint64_t tiles = (n + TB - 1) / TB;
+    const uint64_t tiles = (n + TILE - 1) / TILE;
     const uint64_t cap = (uint64_t)num_sms();
     k_mlp_grad<<<(unsigned)(tiles < cap ? tiles : cap), TB, smem, s>>>(
         reinterpret_cast<const __nv_bfloat16 *>(Wb), X, T, n, scale, grad, loss);
