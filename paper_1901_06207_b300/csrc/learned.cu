@@ -146,13 +146,15 @@ __global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16 *__rest
 // reductions); then every thread accumulates its share of the weight
 // gradients over the tile's samples in registers, and adds them to `grad`
 // once at the end.  Small tiles spread a batch over many SMs (a 4096-sample
-// batch fills 128 blocks).
-constexpr int TB = 128;
+// batch fills 128 blocks of eight warps).
+constexpr int TB = 256;
 constexpr int TILE = 32;
 constexpr int PARTS = TB / TILE;
 constexpr int HP = HID / PARTS;
 constexpr int LD = TILE + 1;
-static_assert(TB % TILE == 0 && HID % PARTS == 0, "tile split");
+constexpr int R2 = HID * HID / TB;     // W2 rows of one column a thread accumulates
+constexpr int R1 = HID * IN / TB;      // W1 rows of one column a thread accumulates
+static_assert(TB % TILE == 0 && HID % PARTS == 0 && TB % HID == 0 && TB % IN == 0 && TB > HID, "tile split");
 
 __global__ void __launch_bounds__(TB) k_mlp_grad(const __nv_bfloat16 *__restrict__ Wb, const float *__restrict__ X,
                                                  const float *__restrict__ Tgt, uint64_t n, float scale,
@@ -169,13 +171,13 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(const __nv_bfloat16 *__restrict
     load_weights(Wb, w);
     const int k = threadIdx.x;
     const int sl = k % TILE, i0 = (k / TILE) * HP;   // this thread's sample in the tile, first hidden unit
-    // register accumulators: W2 rows ib2*32.. of column j2, W1 rows ib1*8.. of column j1
-    const int j2 = k & 63, ib2 = k >> 6, j1 = k & 15, ib1 = k >> 4;
-    float g2[32], g1[8];
+    // register accumulators: W2 rows ib2*R2.. of column j2, W1 rows ib1*R1.. of column j1
+    const int j2 = k % HID, ib2 = k / HID, j1 = k % IN, ib1 = k / IN;
+    float g2[R2], g1[R1];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) g2[q] = 0.f;
+    for (int q = 0; q < R2; ++q) g2[q] = 0.f;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) g1[q] = 0.f;
+    for (int q = 0; q < R1; ++q) g1[q] = 0.f;
     float gw3 = 0.f, gb2 = 0.f, gb1 = 0.f, gb3 = 0.f, lsum = 0.f;
     __syncthreads();
     const uint64_t tiles = (n + TILE - 1) / TILE;
@@ -230,10 +232,10 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(const __nv_bfloat16 *__restrict
         for (int t = 0; t < TILE; ++t) {
             const float h1 = H1[j2 * LD + t];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) g2[q] = fmaf(D2[(ib2 * 32 + q) * LD + t], h1, g2[q]);
+            for (int q = 0; q < R2; ++q) g2[q] = fmaf(D2[(ib2 * R2 + q) * LD + t], h1, g2[q]);
             const float xv = Xs[j1 * LD + t];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) g1[q] = fmaf(D1[(ib1 * 8 + q) * LD + t], xv, g1[q]);
+            for (int q = 0; q < R1; ++q) g1[q] = fmaf(D1[(ib1 * R1 + q) * LD + t], xv, g1[q]);
             if (k < HID) {
                 gw3 = fmaf(D3[t], H2[k * LD + t], gw3);
                 gb2 += D2[k * LD + t];
@@ -245,9 +247,9 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(const __nv_bfloat16 *__restrict
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 32; ++q) atomicAdd(&grad[OW2 + (ib2 * 32 + q) * HID + j2], g2[q]);
+    for (int q = 0; q < R2; ++q) atomicAdd(&grad[OW2 + (ib2 * R2 + q) * HID + j2], g2[q]);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) atomicAdd(&grad[OW1 + (ib1 * 8 + q) * IN + j1], g1[q]);
+    for (int q = 0; q < R1; ++q) atomicAdd(&grad[OW1 + (ib1 * R1 + q) * IN + j1], g1[q]);
     if (k < HID) {
         atomicAdd(&grad[OW3 + k], gw3);
         atomicAdd(&grad[OB2 + k], gb2);
