@@ -300,7 +300,10 @@ int cbaa_detect(const cbaa_cube *cube, uint32_t theta, void *dev_ws, size_t ws_b
  * output records (dev_out, room for cap) and dev_info.
  *  - The first call on a device looks the array up on that device (make
  *    that device current, and make this first call before any stream
- *    capture).
+ *    capture).  The address found is kept for the life of the process, so
+ *    do not use this entry point on a device after cudaDeviceReset (or
+ *    any other teardown of its primary context): the kept address would
+ *    no longer be valid there.
  *  - The call clears the scratch state it relies on, but all calls share
  *    one array: calls that overlap on the GPU (other streams, other host
  *    threads, the same device) race and give wrong results.

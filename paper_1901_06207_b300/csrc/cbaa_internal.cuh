@@ -134,6 +134,15 @@ namespace cbaa {
 // library returns goes through it.
 int cuda_status(cudaError_t e);
 int num_sms();   // SM count of the current device (cached on first use)
+// Opts kernel `fn` into `bytes` of dynamic shared memory on the current
+// device, once per (kernel, device) and again only when more is asked for,
+// so launches on the hot path (and launches recorded into a CUDA graph) do
+// not repeat the attribute call.
+cudaError_t allow_smem_fn(const void *fn, size_t bytes);
+template <typename K>
+inline cudaError_t allow_smem(K kernel, size_t bytes) {
+    return allow_smem_fn(reinterpret_cast<const void *>(kernel), bytes);
+}
 cudaError_t launch_update(const Geo &G, uint32_t *cube, const uint32_t *pairs, size_t n, uint32_t blocks_per_sm,
                           cudaStream_t s);
 // dst |= OR(srcs); assign: dst = OR(srcs) (dst is not read).

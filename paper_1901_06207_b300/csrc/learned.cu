@@ -328,7 +328,7 @@ cudaError_t launch_mlp_grad(const uint16_t *Wb, const float *X, const float *T, 
                             float *grad, float *loss, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const size_t smem = mlp_grad_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(k_mlp_grad, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + TILE - 1) / TILE;
     const uint64_t cap = (uint64_t)num_sms();

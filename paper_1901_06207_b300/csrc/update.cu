@@ -9,6 +9,7 @@
 // the cube out of L2; the cube itself is left with the default policy and
 // stays L2-resident when it fits.
 #include <atomic>
+#include <mutex>
 
 #include "cbaa_internal.cuh"
 
@@ -253,6 +254,30 @@ int num_sms() {
         g_num_sms.store(n, std::memory_order_relaxed);
     }
     return n;
+}
+
+static std::mutex g_smem_mu;
+struct SmemGrant { const void *fn; int dev; size_t bytes; };
+static SmemGrant g_smem[256];
+static int g_smem_n = 0;
+
+cudaError_t allow_smem_fn(const void *fn, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    int i = 0;
+    for (; i < g_smem_n; ++i)
+        if (g_smem[i].fn == fn && g_smem[i].dev == dev) break;
+    if (i < g_smem_n && g_smem[i].bytes >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (i == g_smem_n) {
+        if (g_smem_n < 256) g_smem[g_smem_n++] = {fn, dev, bytes};   // else set, just not remembered
+    } else {
+        g_smem[i].bytes = bytes;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------

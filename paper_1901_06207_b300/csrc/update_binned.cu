@@ -29,8 +29,6 @@
 //                      into the tile's cube
 // Traffic per packet: 8 B read twice (count, scatter), 4 B per code
 // written and read once.
-#include <mutex>
-
 #include "cbaa_internal.cuh"
 #include "update_binned.h"
 
@@ -295,36 +293,6 @@ __global__ void __launch_bounds__(kApplyThreads) k_bin_apply(const BinSegs S, ui
         }
         __syncthreads();
     }
-}
-
-// Opt a kernel into `bytes` of dynamic shared memory once per device and
-// kernel (again only if a larger size is asked for), so that launches
-// recorded into a CUDA graph do not repeat the attribute call.
-std::mutex g_smem_mu;
-struct SmemGrant { const void *fn; int dev; size_t bytes; };
-SmemGrant g_smem[128];
-int g_smem_n = 0;
-
-template <typename K>
-cudaError_t allow_smem(K kernel, size_t bytes) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const void *fn = reinterpret_cast<const void *>(kernel);
-    std::lock_guard<std::mutex> lock(g_smem_mu);
-    int i = 0;
-    for (; i < g_smem_n; ++i)
-        if (g_smem[i].fn == fn && g_smem[i].dev == dev) break;
-    if (i < g_smem_n && g_smem[i].bytes >= bytes) return cudaSuccess;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    if (i == g_smem_n) {
-        if (g_smem_n == 128) return cudaSuccess;       // table full: the attribute is set, just not remembered
-        g_smem[g_smem_n++] = {fn, dev, bytes};
-    } else {
-        g_smem[i].bytes = bytes;
-    }
-    return cudaSuccess;
 }
 
 template <int NRA, int NVA, int THREADS, int PPT>

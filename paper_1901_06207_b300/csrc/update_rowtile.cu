@@ -23,8 +23,6 @@
 //                     flush it; then the overflow list, by direct reductions
 // Traffic per packet: 8 B read once (plus 8 B more when every packet is
 // counted), a 4-byte (r >= 5) or 8-byte record written and read once.
-#include <mutex>
-
 #include "cbaa_internal.cuh"
 #include "update_binned.h"
 
@@ -459,32 +457,6 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
         const uint64_t c = c0 + threadIdx.x;
         if (c < n_ovf) overflow_entry<SHORT>(G, S, ovf[c]);
     }
-}
-
-std::mutex g_attr_mu;
-struct Grant { const void *fn; int dev; size_t bytes; };
-Grant g_grants[64];
-int g_ngrants = 0;
-
-template <typename K>
-cudaError_t allow_smem(K kernel, size_t bytes) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const void *fn = reinterpret_cast<const void *>(kernel);
-    std::lock_guard<std::mutex> lock(g_attr_mu);
-    int i = 0;
-    for (; i < g_ngrants; ++i)
-        if (g_grants[i].fn == fn && g_grants[i].dev == dev) break;
-    if (i < g_ngrants && g_grants[i].bytes >= bytes) return cudaSuccess;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    if (i == g_ngrants) {
-        if (g_ngrants < 64) g_grants[g_ngrants++] = {fn, dev, bytes};
-    } else {
-        g_grants[i].bytes = bytes;
-    }
-    return cudaSuccess;
 }
 
 // Overflow list of a sampled pass (null: exact counts, no overflow).

@@ -113,6 +113,8 @@ class Server:
         self.stats = dict(admitted=0, queued_for_cube=0, queued_for_slot=0, max_cubes_in_use=0, batches=0,
                           updates=0)
         self.lookahead = lookahead
+        self.opened = {}                        # tenant -> windows that got a cube (most recent last)
+        self.opened_keep = 4096
 
     # ------------------------------------------------------------------ public API
     def submit(self, tenant, window: int, pairs, arrival_t: float | None = None, poll: bool = True):
@@ -126,7 +128,9 @@ class Server:
             self.poll()
 
     def close(self, tenant, window: int, poll: bool = True):
-        """Mark tenant's window complete: its detect runs once its queued batches are in."""
+        """Mark tenant's window complete: its detect runs once its queued batches are in.  A window that
+        received no batch still yields a result (the detect of an empty cube: no packets, no hosts); a
+        close for a window that a newer window's batch has already closed changes nothing."""
         self.queue.append(_Request(tenant, window, None, -1, time.perf_counter()))
         if poll:
             self.poll()
@@ -174,6 +178,17 @@ class Server:
                 if cur is not None and cur.window == r.window:
                     self.closing.append((r.tenant, cur, time.perf_counter()))
                     del self.open[r.tenant]
+                elif r.window not in self.opened.get(r.tenant, ()):
+                    # a window that received no batch: its result is the detect of an empty cube
+                    cube = self._take_cube()
+                    if cube is None:
+                        self.stats["queued_for_cube"] += 1
+                        blocked_tenants.add(r.tenant)
+                        pending.append(r)
+                        continue
+                    self._mark_opened(r.tenant, r.window)
+                    self.closing.append((r.tenant, _Open(r.window, cube), time.perf_counter()))
+                # else: the window was closed already by a batch of a newer window; its result stands
                 continue
             if cur is None or cur.window != r.window:
                 if cur is not None:                  # a newer window closes the current one
@@ -186,6 +201,7 @@ class Server:
                     pending.append(r)
                     continue
                 cur = self.open[r.tenant] = _Open(r.window, cube)
+                self._mark_opened(r.tenant, r.window)
             slot = next((s for s in self.slots if not s.busy), None)
             if slot is None:
                 self.stats["queued_for_slot"] += 1
@@ -211,6 +227,14 @@ class Server:
             self.stats["batches"] += len(group)
             self.stats["updates"] += 1
         self.queue = pending
+
+    def _mark_opened(self, tenant, window):
+        """Remember that tenant's window got a cube (a close marker for it then never opens an empty one);
+        the most recent `opened_keep` windows per tenant are kept."""
+        seen = self.opened.setdefault(tenant, collections.OrderedDict())
+        seen[window] = True
+        while len(seen) > self.opened_keep:
+            seen.popitem(last=False)
 
     def _absorb(self, r):
         """Later queued batches of r's tenant and window that fill r's slot with it (one copy each, one

@@ -87,9 +87,11 @@ def test_forward_matches_oracle(C):
     assert np.allclose(y, want, rtol=1e-4, atol=1e-4)
 
 
-@pytest.mark.parametrize("n", [1, 127, 3001])
+@pytest.mark.parametrize("n", [1, 127, 3001, 20011])
 def test_gradient_matches_oracle(C, n):
-    """Kernel gradient (FP32 accumulation over tiles of 128, ragged tail) vs fp64 backpropagation."""
+    """Kernel gradient (FP32 accumulation over 32-sample tiles, eight threads per sample, ragged tail)
+    vs fp64 backpropagation.  n = 20011 gives every block of the grid (one per SM) several tiles, so
+    the accumulators carried from tile to tile are checked too."""
     est, w64 = _rand_net(C, 5)
     rng = np.random.default_rng(6)
     X = rng.uniform(0, 1, (n, 16)).astype(np.float32)

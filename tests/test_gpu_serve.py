@@ -101,6 +101,33 @@ def test_queued_batches_share_a_slot_update(C, oracle):
         assert np.array_equal(res[w].hosts["ip"], want["ip"]) and np.array_equal(res[w].hosts["z"], want["z"])
 
 
+def test_close_without_batches_yields_an_empty_result(C, oracle):
+    """A window closed without any batch still yields a result: the detect of an empty cube (no
+    packets, no hosts, status OK), even while another window of the tenant is open; a close for a window
+    that a newer window's batch already closed adds nothing."""
+    from paper_1901_06207_b300.serve import Server
+    srv = Server(GEO.TINY2, THETA, n_slots=2, slot_pairs=1 << 16, n_cubes=2, cap=1 << 12)
+    pairs0, pairs2 = _traffic(0, 0), _traffic(0, 2)
+    srv.close(0, 5)                                   # nothing open, never seen: empty result
+    for b in _batches(pairs0, 700):
+        srv.submit(0, 0, _pinned(b))
+    srv.close(0, 1)                                   # window 0 stays open; window 1 got nothing
+    for b in _batches(pairs2, 702):                   # window 2's first batch closes window 0
+        srv.submit(0, 2, _pinned(b))
+    srv.close(0, 0)                                   # already closed by window 2: no second result
+    srv.close(0, 2)
+    res = srv.drain(timeout_s=120)
+    got = sorted((r.window, r.packets, r.hosts.size) for r in res)
+    want0 = oracle.detect(GEO.TINY2, oracle.build_cube(GEO.TINY2, pairs0), THETA)["hosts"]
+    want2 = oracle.detect(GEO.TINY2, oracle.build_cube(GEO.TINY2, pairs2), THETA)["hosts"]
+    assert [w for w, _, _ in got] == [0, 1, 2, 5]
+    by = {r.window: r for r in res}
+    for w in (1, 5):
+        assert by[w].packets == 0 and by[w].hosts.size == 0 and by[w].info["status"] == C.OK
+    assert want0.size > 0 and np.array_equal(by[0].hosts["ip"], want0["ip"])
+    assert np.array_equal(by[2].hosts["ip"], want2["ip"]) and by[2].packets == pairs2.shape[0]
+
+
 def test_serving_budget_and_batch_limits(C):
     from paper_1901_06207_b300.serve import Server
     with pytest.raises(C.CbaaError):
