@@ -126,6 +126,11 @@ typedef struct cbaa_tuning {
                                       are set by direct reductions; needs workspace room for an overflow
                                       list of every packet, else 2); 0 = 3 for passes of >= 8Mi packets,
                                       2 below, column tiles where row tiles are not allowed */
+    uint32_t heavy;                /* partitioned update of one cube with row tiles: the heaviest sources'
+                                      packets are set through one row bitmap per source in shared memory,
+                                      the rest through row tiles.  0 = on for passes of >= 4Mi packets
+                                      (128 KiB of bitmaps per block), 1 = off, 2 = on with 64 KiB of bitmaps
+                                      (half as many sources), 3 = on with 128 KiB */
 } cbaa_tuning;
 
 typedef struct cbaa_cube cbaa_cube;   /* opaque handle: a params copy plus the caller's memory */

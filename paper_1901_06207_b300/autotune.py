@@ -1,7 +1,8 @@
 """Autotuner for the update path and its launch shapes.
 
-Times the direct update (grid sizes) and the partitioned update (routing
-shape x tile-assembly items x counting grid) on the caller's packets with
+Times the direct update (grid sizes) and the partitioned update (tiling x
+routing shape x tile-assembly items x counting grid x heavy-source split) on
+the caller's packets with
 CUDA events, keeps the fastest, sets it process-wide with cbaa_set_tuning
 and caches the choice per (GPU, geometry, packet-count bucket) in a JSON
 file.  Launch shapes never change results, only time.
@@ -28,7 +29,10 @@ def candidates():
     for b in (4, 8, 16, 32):
         yield "direct", dict(direct_blocks_per_sm=b)
     for kind, shape, items, cnt in itertools.product((1, 2, 3), range(9), (4, 8, 16), (4, 8)):
-        yield "binned", dict(tile_kind=kind, scatter_shape=shape, apply_items_per_sm=items, count_blocks_per_sm=cnt)
+        # the heavy-source split serves row tiles only: off, 64 KiB or 128 KiB of bitmaps per block
+        for heavy in ((1,) if kind == 1 else (1, 2, 3)):
+            yield "binned", dict(tile_kind=kind, scatter_shape=shape, apply_items_per_sm=items,
+                                 count_blocks_per_sm=cnt, heavy=heavy)
 
 
 def time_update(cube, pairs, path: str, ws, reps: int = 3) -> float:

@@ -31,16 +31,65 @@ struct BinSegs {
     uint32_t seg_words;       // tiles_per_seg << kBinTileBits: offset between cubes in the tile space
 };
 
+inline size_t bin_align(size_t x) { return (x + 255) / 256 * 256; }
+
+// Heavy-source split of a single-cube pass (update_heavy.cu).  The sources
+// of most packets of a window are few (super hosts and the head of a Zipf
+// law); all |RA|+|VA| columns of a source receive the same row bits (Alg. 1),
+// so a heavy source's packets are gathered in one row bitmap of W words in
+// shared memory and ORed into its columns once.  Tables:
+//   a sample table of 2^15 slots (count, last key) indexed by the top 15 bits of
+//   the mangled address, a lookup image of 2^14 entries (top 14 bits of the
+//   mangled address -> its low 18 bits << 14 | heavy index), the heavy
+//   sources' mangled addresses, their row bitmaps, and counters.
+constexpr uint32_t kHeavyCountBits = 15;
+constexpr uint32_t kHeavyTabBits = 14;
+constexpr uint32_t kHeavyTagBits = 32 - kHeavyTabBits;            // 18
+constexpr uint32_t kHeavyIdxMask = (1u << kHeavyTabBits) - 1u;     // index field of an entry
+constexpr uint32_t kHeavyEmpty = 0xFFFFFFFFu;                      // index field all ones: no source
+constexpr uint32_t kHeavyMax = 1024;                               // heavy sources per pass at most
+constexpr uint32_t kHeavyBitmapMax = 128u << 10;                   // bytes of row bitmaps per block at most
+uint32_t rowtile_bins(const Geo &G, uint32_t n_cubes);             // row tiles of n_cubes cubes
+constexpr uint32_t kHeavyMaxRegions = 1024;                        // split blocks (residual regions) at most
+// counters: [0], [1] heavy sources taken at or above the threshold and in the
+// bin below it, [32 + b] histogram of sample counts by quarter octave, then the
+// entries of each residual region
+constexpr uint32_t kHeavyCtrHist = 32;                             // 128 bins: quarter octaves
+constexpr uint32_t kHeavyHistBins = 128;
+constexpr uint32_t kHeavyCtrRegions = kHeavyCtrHist + kHeavyHistBins;
+constexpr uint32_t kHeavyCtrWords = kHeavyCtrRegions + kHeavyMaxRegions;
+constexpr uint32_t kHeavyRegionAlign = 16384;                      // region capacity unit (largest routing block)
+
+struct HeavyWs {
+    uint32_t *count, *key;        // sample table [2^kHeavyCountBits]
+    uint32_t *tab;                // lookup image [2^kHeavyTabBits]
+    uint32_t *list;               // mangled address of heavy source h [kHeavyMax]
+    uint32_t *bits;               // row bitmaps [kHeavyMax][W]
+    uint32_t *ctr;                // counters [kHeavyCtrWords]
+    uint32_t *rcount() const { return ctr + kHeavyCtrRegions; }
+};
+// Bytes from HeavyWs::count to the end of HeavyWs::ctr (cleared at the start of a pass).
+inline size_t heavy_clear_bytes(const Geo &G) {
+    return bin_align(sizeof(uint32_t) << kHeavyCountBits) + bin_align(sizeof(uint32_t) * (size_t)kHeavyMax * G.W) +
+           sizeof(uint32_t) * kHeavyCtrWords;
+}
+
+inline size_t heavy_ws_bytes(const Geo &G) {
+    return 2 * bin_align(sizeof(uint32_t) << kHeavyCountBits) + bin_align(sizeof(uint32_t) << kHeavyTabBits) +
+           bin_align(sizeof(uint32_t) * kHeavyMax) + bin_align(sizeof(uint32_t) * (size_t)kHeavyMax * G.W) +
+           bin_align(sizeof(uint32_t) * kHeavyCtrWords);
+}
+
 struct BinWs {
     uint32_t *counts, *offsets, *cursors, *item_start, *nchunk, *codes;
     size_t max_pairs;                     // packets routed per pass (codes hold A per packet)
+    uint64_t words;                       // words of the codes buffer (A + 2 per packet sized for)
+    HeavyWs heavy;
 };
-
-inline size_t bin_align(size_t x) { return (x + 255) / 256 * 256; }
 
 // Five tables of nb + 2 words: per-tile counts (counts[nb] and counts[nb + 1]
 // are counters of the row-tile path), offsets, cursors, item starts, chunks.
-inline size_t bin_ws_fixed(uint32_t nb) { return 5 * bin_align(sizeof(uint32_t) * ((size_t)nb + 2)); }
+inline size_t bin_ws_tables_bytes(uint32_t nb) { return 5 * bin_align(sizeof(uint32_t) * ((size_t)nb + 2)); }
 
 // Row tiles (update_rowtile.cu): one per (cube, sketch, row word), each
 // holding one word of every column of its sketch.
@@ -58,18 +107,26 @@ inline uint32_t bin_ws_tables(const Geo &G, uint32_t n_cubes) {
     return col > row ? col : row;
 }
 
+// Words of the code buffer per packet a workspace is sized for: A codes
+// (column tiles), or a residual entry {mangled ip, row} of the heavy split
+// (2 words) plus a record and an overflow entry of the row-tile pass.
+inline size_t bin_ws_words_per_pair(const Geo &G) { return (size_t)G.A + 2; }
+
+inline size_t bin_ws_fixed(const Geo &G, uint32_t nb) { return bin_ws_tables_bytes(nb) + heavy_ws_bytes(G); }
+
 inline size_t bin_ws_bytes(const Geo &G, uint32_t n_cubes, size_t max_pairs) {
-    return bin_ws_fixed(bin_ws_tables(G, n_cubes)) + bin_align(sizeof(uint32_t) * (size_t)G.A * max_pairs);
+    return bin_ws_fixed(G, bin_ws_tables(G, n_cubes)) +
+           bin_align(sizeof(uint32_t) * bin_ws_words_per_pair(G) * max_pairs);
 }
 
 // Carve `bytes` at `base` into a BinWs for n_cubes cubes; false if not even one packet fits.
 inline bool bin_ws_make(const Geo &G, uint32_t n_cubes, void *base, size_t bytes, BinWs *W) {
     const uint32_t nb = bin_ws_tables(G, n_cubes);
-    const size_t fixed = bin_ws_fixed(nb);
-    if (bytes < fixed + sizeof(uint32_t) * G.A) return false;
-    size_t m = (bytes - fixed) / (sizeof(uint32_t) * G.A);
-    const size_t cap = (size_t)(1u << 31) / G.A;            // code offsets stay 32-bit
-    if (m > cap) m = cap;
+    const size_t fixed = bin_ws_fixed(G, nb);
+    const size_t per = bin_ws_words_per_pair(G);
+    if (bytes < fixed + sizeof(uint32_t) * per) return false;
+    uint64_t words = (bytes - fixed) / sizeof(uint32_t);
+    if (words > (1ull << 31)) words = 1ull << 31;            // code offsets stay 32-bit
     char *b = static_cast<char *>(base);
     const size_t step = bin_align(sizeof(uint32_t) * ((size_t)nb + 2));
     W->counts = reinterpret_cast<uint32_t *>(b);
@@ -77,8 +134,22 @@ inline bool bin_ws_make(const Geo &G, uint32_t n_cubes, void *base, size_t bytes
     W->cursors = reinterpret_cast<uint32_t *>(b + 2 * step);
     W->item_start = reinterpret_cast<uint32_t *>(b + 3 * step);
     W->nchunk = reinterpret_cast<uint32_t *>(b + 4 * step);
+    // what a pass clears first (sample counts, row bitmaps, counters) lies in one run
+    char *h = b + bin_ws_tables_bytes(nb);
+    W->heavy.count = reinterpret_cast<uint32_t *>(h);
+    h += bin_align(sizeof(uint32_t) << kHeavyCountBits);
+    W->heavy.bits = reinterpret_cast<uint32_t *>(h);
+    h += bin_align(sizeof(uint32_t) * (size_t)kHeavyMax * G.W);
+    W->heavy.ctr = reinterpret_cast<uint32_t *>(h);
+    h += bin_align(sizeof(uint32_t) * kHeavyCtrWords);
+    W->heavy.key = reinterpret_cast<uint32_t *>(h);
+    h += bin_align(sizeof(uint32_t) << kHeavyCountBits);
+    W->heavy.tab = reinterpret_cast<uint32_t *>(h);
+    h += bin_align(sizeof(uint32_t) << kHeavyTabBits);
+    W->heavy.list = reinterpret_cast<uint32_t *>(h);
     W->codes = reinterpret_cast<uint32_t *>(b + fixed);
-    W->max_pairs = m;
+    W->words = words;
+    W->max_pairs = words / G.A;                               // column tiles: A codes per packet
     return true;
 }
 
@@ -86,6 +157,30 @@ cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, c
                                    cudaStream_t s);
 cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                                   cudaStream_t s);
+// Residual of the heavy split: region b holds rcount[b] entries {mangled
+// ip, row} from entry b * rcap on (rcap a multiple of kHeavyRegionAlign),
+// nreg regions.
+struct Residual {
+    const uint2 *entries;
+    const uint32_t *rcount;
+    uint64_t rcap;
+    uint32_t nreg;
+};
+// One row-tile pass over the residual entries of the heavy split (m of them
+// at most), with run capacities from a sample when `sampled`; W.codes /
+// W.words: the room after the residual regions.  W.counts[0 .. nb] must be
+// zero already (the split's histogram kernel clears them).
+cudaError_t rowtile_pass_hashed(const Geo &G, uint32_t *cube, const Residual &R, uint64_t m, const BinWs &W,
+                                const cbaa_tuning &T, bool sampled, cudaStream_t s);
+// Words a row-tile pass of m packets needs in the code buffer (sampled run
+// capacities with their overflow list, or exact counts).
+uint64_t rowtile_pass_words(const Geo &G, uint64_t m, bool sampled);
+constexpr uint64_t kRowTileMinSampled = 8ull << 20;  // below this every packet is counted
+// Heavy-source split in front of the row tiles (single cube, update_heavy.cu).
+cudaError_t launch_update_heavy(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint64_t n, const BinWs &W,
+                                const cbaa_tuning &T, cudaStream_t s);
+// Whether the split serves a pass over these cubes with this tuning.
+bool heavy_enabled(const Geo &G, uint32_t n_cubes, uint64_t n, const cbaa_tuning &T);
 cudaError_t launch_bin_scan(uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s,
                             uint32_t samp = 1);
 

@@ -1,0 +1,482 @@
+// Alg. 1 with the heavy sources split off: a pre-pass in front of the
+// row-tile update for single-cube passes.
+//
+// All |RA|+|VA| bits that a packet sets share its sketch and its row, and
+// its columns depend on its source alone (Alg. 1: the CS and the column
+// indices come from the mangled inner address, the row from H_bv of the
+// outer one).  So the bits that one source sets over a window are its set
+// of rows, the same in each of its columns: a row bitmap of W words.  On
+// core-network traffic a few sources carry most packets (super hosts and
+// the head of a Zipf law), so:
+//
+//   1. k_heavy_sample : one tile of 1024 packets in 128 is counted by the top
+//                       15 bits of the mangled address (with the last
+//                       address seen in each slot)
+//   2. k_heavy_hist, k_heavy_select : the most counted slots, up to K of
+//                       them, become the heavy sources; a lookup table maps a
+//                       mangled address to its heavy index (top 13 bits ->
+//                       low 19 bits as a tag and the index)
+//   3. k_heavy_split  : every packet: a heavy source's row bit is set in
+//                       its bitmap in shared memory (a bit already set is
+//                       only read); any other packet is written out as
+//                       {mangled ip, row}.  Each block ORs its bitmaps into
+//                       the global ones with one bulk reduction.
+//   4. k_heavy_expand : each heavy bitmap is ORed into the source's columns
+//   5. the row-tile pass over the residual entries (update_rowtile.cu)
+//
+// Which sources are heavy only decides the path a packet takes, never the
+// cube: every packet's bits are set by one of the two paths.
+#include <cstring>
+
+#include "cbaa_internal.cuh"
+#include "update_binned.h"
+
+namespace cbaa {
+
+namespace {
+
+constexpr uint32_t kSampleThreads = 1024;
+constexpr uint32_t kSampleTile = 1024;                 // packets of a sample tile, one per thread
+constexpr uint32_t kHeavySampleEvery = 128;            // one sample tile in 128
+constexpr uint32_t kHeavyMinCount = 4;                 // sampled packets a heavy source needs at least
+constexpr uint64_t kHeavyMinPackets = 4ull << 20;      // default: passes of at least this many packets
+constexpr uint32_t kTabWords = 1u << kHeavyTabBits;
+constexpr uint32_t kCountSlots = 1u << kHeavyCountBits;
+constexpr uint32_t kTagMask = (1u << kHeavyTagBits) - 1u;
+
+__device__ __forceinline__ uint4 ld_quad_nc(const uint32_t *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_pair_nc(const uint32_t *p) {
+    uint2 v;
+    asm volatile("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
+    asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Heavy index of mangled address m, or kHeavyIdxMask.  d = entry ^ (tag of
+// m << 13) keeps only the index field exactly when the tags agree, and the
+// empty marker's index field is all ones.
+__device__ __forceinline__ uint32_t heavy_index(const uint32_t *tab, uint32_t m) {
+    const uint32_t d = tab[m >> kHeavyTagBits] ^ ((m & kTagMask) << kHeavyTabBits);
+    return d < kHeavyIdxMask ? d : kHeavyIdxMask;
+}
+
+// Counts of the sample by slot, first in shared memory (one table per
+// block, 2^15 counters), then added to the global table: a heavy source's
+// slot gets one global atomic per block instead of one per sampled packet.
+// Sampled tile j (1024 consecutive packets, one per thread) starts at packet
+// j * 1024 * 128.
+template <bool ORIENT>
+__global__ void __launch_bounds__(kSampleThreads, 1) k_heavy_sample(const Geo G, const uint32_t *__restrict__ pairs,
+                                                                    uint64_t n, uint32_t *__restrict__ count,
+                                                                    uint32_t *__restrict__ key) {
+    extern __shared__ __align__(16) uint32_t cnt[];
+    for (uint32_t i = threadIdx.x; i < kCountSlots / 4; i += kSampleThreads)
+        reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const uint64_t tiles = (n + (uint64_t)kSampleTile * kHeavySampleEvery - 1) / ((uint64_t)kSampleTile * kHeavySampleEvery);
+    // four sampled tiles per step (tiles j + u * gridDim.x), their loads in flight together
+    for (uint64_t j = blockIdx.x; j < tiles; j += 4ull * gridDim.x) {
+        uint2 v[4];
+        bool have[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint64_t p = (j + (uint64_t)u * gridDim.x) * kSampleTile * kHeavySampleEvery + threadIdx.x;
+            have[u] = p < n;
+            if (have[u]) v[u] = ld_pair_nc(pairs + 2 * p);
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            if (!have[u]) continue;
+            if (ORIENT && !orient(G, v[u].x, v[u].y)) continue;
+            const uint32_t m = mangle(G, v[u].x);
+            const uint32_t slot = m >> (32 - kHeavyCountBits);
+            // the slot keeps an address seen at every 8th count of a block: a slot with
+            // one heavy source keeps that source's address with high probability
+            if ((atomicAdd(&cnt[slot], 1u) & 7u) == 0u) key[slot] = m;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kCountSlots; i += kSampleThreads) {
+        const uint32_t c = cnt[i];
+        if (c) atomicAdd(&count[i], c);
+    }
+}
+
+// Quarter-octave bin of a sample count: 4 floor(log2 c) + the two bits below
+// the leading one, or kHeavyHistBins below kHeavyMinCount (4, so e >= 2).
+__device__ __forceinline__ uint32_t count_bin(uint32_t c) {
+    if (c < kHeavyMinCount) return kHeavyHistBins;
+    const uint32_t e = 31 - __clz(c);
+    return 4 * e + ((c >> (e - 2)) & 3u);
+}
+// Smallest count of bin b.
+__device__ __forceinline__ uint32_t bin_floor(uint32_t b) { return (4u + (b & 3u)) << ((b >> 2) - 2); }
+
+// Histogram of the sample counts by quarter octave (one slot per thread).
+// Also readies what the pass uses next: the lookup table empty (kTabWords
+// entries spread over the blocks) and the row-tile counts zero (nzero words).
+__global__ void __launch_bounds__(1024) k_heavy_hist(const uint32_t *__restrict__ count, uint32_t *__restrict__ hist,
+                                                     uint32_t *__restrict__ tab, uint32_t *__restrict__ zero,
+                                                     uint32_t nzero) {
+    __shared__ uint32_t h[kHeavyHistBins];
+    if (threadIdx.x < kHeavyHistBins) h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t b = i < kCountSlots ? count_bin(__ldcg(count + i)) : kHeavyHistBins;
+    if (b < kHeavyHistBins) atomicAdd(&h[b], 1u);
+    for (uint32_t t = i; t < kTabWords; t += gridDim.x * blockDim.x) tab[t] = kHeavyEmpty;
+    for (uint32_t t = i; t < nzero; t += gridDim.x * blockDim.x) zero[t] = 0u;
+    __syncthreads();
+    if (threadIdx.x < kHeavyHistBins && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// Heavy sources (one slot per thread): every slot counted at least thr
+// times, thr the smallest bin floor that selects at most kmax slots, then
+// slots of the bin below thr while room is left.  Upper slots take indices
+// [0, acc) from ctr[0], the others acc + ctr[1] (dropped from kmax on).  Two
+// sources whose lookup entries collide: the one that loses the CAS stays on
+// the row-tile path.  tab starts all empty.
+__global__ void __launch_bounds__(1024) k_heavy_select(const uint32_t *__restrict__ count,
+                                                       const uint32_t *__restrict__ key, uint32_t kmax,
+                                                       uint32_t *__restrict__ tab, uint32_t *__restrict__ list,
+                                                       uint32_t *__restrict__ ctr) {
+    __shared__ uint32_t s_thr, s_lo, s_acc;
+    __shared__ uint32_t hist[kHeavyHistBins];
+    if (threadIdx.x < kHeavyHistBins) hist[threadIdx.x] = __ldcg(ctr + kHeavyCtrHist + threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {                            // from shared memory: no global round trip per bin
+        uint32_t acc = 0, thr = 0xFFFFFFFFu, lo = 0xFFFFFFFFu;
+        for (int b = (int)kHeavyHistBins - 1; b >= 0; --b) {
+            const uint32_t hb = hist[b];
+            if (acc + hb > kmax) {                     // this bin only partly, while room is left
+                lo = hb ? bin_floor(b) : lo;
+                break;
+            }
+            acc += hb;
+            if (hb) thr = bin_floor(b);
+        }
+        s_thr = thr;
+        s_lo = lo < thr ? lo : thr;
+        s_acc = acc;
+    }
+    __syncthreads();
+    const uint32_t thr = s_thr, lo = s_lo, acc = s_acc, lane = threadIdx.x & 31u;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t c = i < kCountSlots ? __ldcg(count + i) : 0u;
+    const bool up = c >= thr && c >= kHeavyMinCount, low = !up && c >= lo && c >= kHeavyMinCount;
+    // one reservation per warp for each kind
+    const uint32_t wu = __ballot_sync(0xffffffffu, up), wl = __ballot_sync(0xffffffffu, low);
+    uint32_t fu = 0, fl = 0;
+    if (wu && lane == __ffs(wu) - 1) fu = atomicAdd(ctr + 0, __popc(wu));
+    if (wl && lane == __ffs(wl) - 1) fl = atomicAdd(ctr + 1, __popc(wl));
+    fu = wu ? __shfl_sync(0xffffffffu, fu, __ffs(wu) - 1) : 0u;
+    fl = wl ? __shfl_sync(0xffffffffu, fl, __ffs(wl) - 1) : 0u;
+    if (!up && !low) return;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t h = up ? fu + __popc(wu & below) : acc + fl + __popc(wl & below);
+    if (h >= kmax) return;                              // the partial bin only while room is left
+    const uint32_t k = __ldcg(key + i);
+    list[h] = k;
+    atomicCAS(&tab[k >> kHeavyTagBits], kHeavyEmpty, ((k & kTagMask) << kHeavyTabBits) | h);
+}
+
+// Heavy sources taken: the upper ones plus the lower ones that found room.
+__device__ __forceinline__ uint32_t heavy_count(const uint32_t *ctr, uint32_t kmax) {
+    const uint32_t t = ctr[0] + ctr[1];
+    return t < kmax ? t : kmax;
+}
+
+// Packets of chunk c (32 lanes x 8 packets, 2 per 16-byte load) into q;
+// ok: bit k set when slot k of this lane holds a packet.  Slot 2j + h of lane
+// l is packet c * 256 + 2 (l + 32 j) + h.
+__device__ __forceinline__ uint32_t split_load(const uint32_t *pairs, uint64_t n, uint64_t c, uint32_t lane,
+                                               bool al, uint4 (&q)[4]) {
+    const uint64_t c0 = c * 256;
+    if (al && c0 + 256 <= n) {
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) q[j] = ld_quad_nc(pairs + 2 * c0 + 4 * (lane + 32 * j));
+        return 0xFFu;
+    }
+    uint32_t ok = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        const uint64_t p = c0 + 2 * (lane + 32 * j);
+        q[j] = make_uint4(0u, 0u, 0u, 0u);
+        if (p < n) {
+            const uint2 a = ld_pair_nc(pairs + 2 * p);
+            q[j].x = a.x;
+            q[j].y = a.y;
+            ok |= 1u << (2 * j);
+        }
+        if (p + 1 < n) {
+            const uint2 b = ld_pair_nc(pairs + 2 * (p + 1));
+            q[j].z = b.x;
+            q[j].w = b.y;
+            ok |= 2u << (2 * j);
+        }
+    }
+    return ok;
+}
+
+// Every warp walks its own chunks of 256 packets (chunk c for c = global
+// warp, + all warps, ...), the next chunk's loads in flight while it works
+// on the current one.  Shared memory: the lookup table, then K row bitmaps
+// of W words (kwords words).  Residual entries go to this block's region
+// (rcap entries from blockIdx.x * rcap), one shared-memory reservation per
+// warp and chunk; the region's count is written at the end.
+template <uint32_t THREADS, uint32_t MINB, bool ORIENT>
+__global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, const uint32_t *__restrict__ pairs,
+                                                               uint64_t n, const uint32_t *__restrict__ tab_g,
+                                                               uint32_t kwords, uint32_t *__restrict__ bits_g,
+                                                               uint2 *__restrict__ resid, uint64_t rcap,
+                                                               uint32_t *__restrict__ rcount) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *tab = sm;
+    uint32_t *bm = sm + kTabWords;
+    __shared__ uint32_t s_cnt;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(tab_g);
+        uint4 *dst = reinterpret_cast<uint4 *>(tab);
+        for (uint32_t i = tid; i < kTabWords / 4; i += THREADS) dst[i] = __ldg(src + i);
+        uint4 *b4 = reinterpret_cast<uint4 *>(bm);
+        for (uint32_t i = tid; i < kwords / 4; i += THREADS) b4[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (tid == 0) s_cnt = 0;
+    }
+    __syncthreads();
+    uint2 *region = resid + (uint64_t)blockIdx.x * rcap;
+    const bool al = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
+    const uint64_t chunks = (n + 255) / 256;
+    const uint64_t nw = (uint64_t)gridDim.x * (THREADS / 32);
+    uint64_t c = (uint64_t)blockIdx.x * (THREADS / 32) + (tid >> 5);
+    uint4 q[4], qn[4];
+    uint32_t ok = c < chunks ? split_load(pairs, n, c, lane, al, q) : 0u;
+    for (; c < chunks; c += nw) {
+        const uint32_t okn = c + nw < chunks ? split_load(pairs, n, c + nw, lane, al, qn) : 0u;
+        // in phases, so that the eight packets' shared-memory reads are in flight together:
+        // hashes; lookups; bitmap words of the heavy ones; sets of the bits still clear
+        uint32_t m[8], row[8], h[8];
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) {
+            uint32_t a = (k & 1u) ? q[k / 2].z : q[k / 2].x;
+            uint32_t b = (k & 1u) ? q[k / 2].w : q[k / 2].y;
+            if (ORIENT && ((ok >> k) & 1u) && !orient(G, a, b)) ok &= ~(1u << k);   // raw {src, dst} against NI
+            m[k] = mangle(G, a);
+            row[k] = row_of(G, b);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) h[k] = heavy_index(tab, m[k]);
+        uint32_t heavy = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) {
+            if (((ok >> k) & 1u) && h[k] < kHeavyIdxMask) {
+                heavy |= 1u << k;
+                h[k] = h[k] * G.W + (row[k] >> 5);            // the bitmap word
+            }
+        }
+        uint32_t wv[8];
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) wv[k] = ((heavy >> k) & 1u) ? bm[h[k]] : 0xFFFFFFFFu;
+        // a stale read only costs an atomic that changes nothing: every set is an OR
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) {
+            const uint32_t bit = 1u << (row[k] & 31u);
+            if (!(wv[k] & bit)) atomicOr(&bm[h[k]], bit);
+        }
+        const uint32_t keep = ok & ~heavy;
+        const uint32_t cnt = __popc(keep);
+        // this warp's entries: lane prefix, one reservation in the block's region
+        uint32_t x = cnt;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t base = 0;
+        if (lane == 31 && x) base = atomicAdd(&s_cnt, x);
+        base = __shfl_sync(0xffffffffu, base, 31) + x - cnt;
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k)
+            if ((keep >> k) & 1u) region[base + __popc(keep & ((1u << k) - 1u))] = make_uint2(m[k], row[k]);
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) q[j] = qn[j];
+        ok = okn;
+    }
+    // the region's count, then the block's bitmaps into the global ones: one
+    // bulk OR reduction (async proxy), after the shared-memory writes are
+    // made visible to it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+        rcount[blockIdx.x] = s_cnt;
+        constexpr uint32_t kChunk = 32u << 10;
+        const uint32_t bytes = kwords * 4u;
+        const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(bm));
+        for (uint32_t off = 0; off < bytes; off += kChunk) {
+            const uint32_t len = bytes - off < kChunk ? bytes - off : kChunk;
+            asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.or.b32 [%0], [%1], %2;"
+                         :: "l"(reinterpret_cast<char *>(bits_g) + off), "r"(s0 + off), "r"(len) : "memory");
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+}
+
+// One warp per (heavy source, array): the source's row bitmap ORed into its
+// column of that array.
+__global__ void __launch_bounds__(256) k_heavy_expand(const Geo G, uint32_t *__restrict__ cube,
+                                                      const uint32_t *__restrict__ list,
+                                                      const uint32_t *__restrict__ ctr, uint32_t kmax,
+                                                      const uint32_t *__restrict__ bits) {
+    const uint32_t nh = heavy_count(ctr, kmax);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = gridDim.x * blockDim.x / 32;
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) / 32; t < nh * G.A; t += warps) {
+        const uint32_t h = t / G.A, a = t - h * G.A;
+        const uint32_t m = list[h], cs = m & G.smask, lp = m >> G.r;
+        const uint32_t col = a < G.n_ra ? ra_col(G, a, lp) : va_col(G, a - G.n_ra, lp);
+        uint32_t *dst = cube + (size_t)cs * G.cs_words + G.arr_base[a] + (size_t)col * G.W;
+        const uint32_t *src = bits + (size_t)h * G.W;
+        for (uint32_t w = lane; w < G.W; w += 32) {
+            const uint32_t x = src[w];
+            if (x) red_or(dst + w, x);
+        }
+    }
+}
+
+uint32_t heavy_budget(const cbaa_tuning &T) { return T.heavy == 2 ? (64u << 10) : kHeavyBitmapMax; }
+
+// Heavy sources that fit the bitmap budget (W words each), at most kHeavyMax.
+uint32_t heavy_sources(const Geo &G, const cbaa_tuning &T) {
+    const uint32_t k = heavy_budget(T) / (4u * G.W);
+    return k < kHeavyMax ? k : kHeavyMax;
+}
+
+// Split blocks: threads and blocks per SM (the lookup table and the bitmaps
+// take most of an SM's shared memory).
+struct SplitShape {
+    uint32_t threads, per_sm;
+};
+SplitShape split_shape(const cbaa_tuning &) { return SplitShape{1024, 1}; }
+
+// Residual regions of a split pass over m packets: one per split block,
+// each as large as the chunks its warps can take, rounded up to kHeavyRegionAlign.
+Residual residual_layout(const cbaa_tuning &T, uint64_t m, const uint32_t *entries_base, const uint32_t *rcount) {
+    const SplitShape sh = split_shape(T);
+    const uint64_t chunks = (m + 255) / 256;
+    const uint64_t wpb = sh.threads / 32;
+    // at least a region's worth of packets per block, so that rounding regions up wastes little
+    uint64_t blocks = (uint64_t)num_sms() * sh.per_sm;
+    const uint64_t need = (m + kHeavyRegionAlign - 1) / kHeavyRegionAlign;
+    if (need < blocks) blocks = need;
+    if (blocks > kHeavyMaxRegions) blocks = kHeavyMaxRegions;
+    if (blocks == 0) blocks = 1;
+    const uint64_t nw = blocks * wpb;
+    const uint64_t per_warp = (chunks + nw - 1) / nw;
+    const uint64_t rcap = (wpb * per_warp * 256 + kHeavyRegionAlign - 1) / kHeavyRegionAlign * kHeavyRegionAlign;
+    return Residual{reinterpret_cast<const uint2 *>(entries_base), rcount, rcap, (uint32_t)blocks};
+}
+
+template <uint32_t THREADS, uint32_t MINB, bool ORIENT>
+cudaError_t launch_split(const Geo &G, const uint32_t *pairs, uint64_t m, const BinWs &W, uint32_t kwords,
+                         const Residual &R, cudaStream_t s) {
+    auto k = k_heavy_split<THREADS, MINB, ORIENT>;
+    const size_t smem = sizeof(uint32_t) * ((size_t)kTabWords + kwords);
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<R.nreg, THREADS, smem, s>>>(G, pairs, m, W.heavy.tab, kwords, W.heavy.bits,
+                                    const_cast<uint2 *>(R.entries), R.rcap, W.heavy.rcount());
+    return cudaGetLastError();
+}
+
+template <bool ORIENT>
+cudaError_t heavy_pass(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint64_t m, const BinWs &W,
+                       const cbaa_tuning &T, bool sampled, cudaStream_t s) {
+    const uint32_t K = heavy_sources(G, T);
+    const uint32_t kwords = K * G.W;
+    const int sms = num_sms();
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(W.heavy.count, 0, heavy_clear_bytes(G), s)) != cudaSuccess) return e;
+    const size_t count_smem = sizeof(uint32_t) * kCountSlots;
+    if ((e = allow_smem(k_heavy_sample<ORIENT>, count_smem)) != cudaSuccess) return e;
+    const uint64_t tiles = (m + (uint64_t)kSampleTile * kHeavySampleEvery - 1) / ((uint64_t)kSampleTile * kHeavySampleEvery);
+    k_heavy_sample<ORIENT><<<(unsigned)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms), kSampleThreads, count_smem, s>>>(
+        G, pairs, m, W.heavy.count, W.heavy.key);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const uint32_t nb = rowtile_bins(G, 1);
+    k_heavy_hist<<<kCountSlots / 1024, 1024, 0, s>>>(W.heavy.count, W.heavy.ctr + kHeavyCtrHist, W.heavy.tab,
+                                                     W.counts, nb + 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_heavy_select<<<kCountSlots / 1024, 1024, 0, s>>>(W.heavy.count, W.heavy.key, K, W.heavy.tab, W.heavy.list,
+                                                      W.heavy.ctr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const Residual R = residual_layout(T, m, W.codes, W.heavy.rcount());
+    e = launch_split<1024, 1, ORIENT>(G, pairs, m, W, kwords, R, s);
+    if (e != cudaSuccess) return e;
+    const uint64_t ewarps = (uint64_t)K * G.A;
+    const uint64_t eblocks = (ewarps * 32 + 255) / 256;
+    const uint64_t ecap = (uint64_t)sms * 8;
+    k_heavy_expand<<<(unsigned)(eblocks < ecap ? eblocks : ecap), 256, 0, s>>>(G, cube, W.heavy.list, W.heavy.ctr,
+                                                                             K, W.heavy.bits);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the residual's row-tile pass in the room after the residual regions
+    const uint64_t rw = 2 * (uint64_t)R.nreg * R.rcap;
+    BinWs W2 = W;
+    W2.codes = W.codes + rw;
+    W2.words = W.words - rw;
+    return rowtile_pass_hashed(G, cube, R, m, W2, T, sampled, s);     // its counts were zeroed by k_heavy_hist
+}
+
+}  // namespace
+
+bool heavy_enabled(const Geo &G, uint32_t n_cubes, uint64_t n, const cbaa_tuning &T) {
+    if (T.heavy == 1 || n_cubes != 1 || T.tile_kind == 1 || !rowtile_ok(G, 1)) return false;
+    if (heavy_sources(G, T) < 16) return false;
+    return T.heavy >= 2 || n >= kHeavyMinPackets;
+}
+
+cudaError_t launch_update_heavy(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint64_t n, const BinWs &W,
+                                const cbaa_tuning &T, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    // Largest pass that fits the code buffer: the residual entries (2 words per
+    // packet) and the row-tile pass over them, whose run capacities come from a
+    // sample as in the plain row-tile path (tile_kind 3, or 0 for passes of at
+    // least kRowTileMinSampled packets) unless that leaves passes too small.
+    auto fit = [&](bool sampled) -> uint64_t {
+        auto need = [&](uint64_t m) {
+            const Residual R = residual_layout(T, m, nullptr, nullptr);
+            return 2 * (uint64_t)R.nreg * R.rcap + rowtile_pass_words(G, m, sampled);
+        };
+        if (need(n) <= W.words) return n;
+        uint64_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const uint64_t mid = lo + (hi - lo) / 2;
+            if (need(mid) <= W.words) lo = mid; else hi = mid;
+        }
+        return lo >= 1024 ? (lo & ~(uint64_t)1023) : lo;   // whole chunks keep later passes 16-byte aligned
+    };
+    bool sampled = T.tile_kind == 3 || (T.tile_kind == 0 && n >= kRowTileMinSampled);
+    uint64_t mmax = sampled ? fit(true) : 0;
+    const uint64_t counted = fit(false);
+    if (sampled && mmax < (T.tile_kind == 3 ? (n < (1u << 16) ? n : (1u << 16)) : counted)) sampled = false;
+    if (!sampled) mmax = counted;
+    if (mmax == 0) return cudaErrorInvalidValue;       // not reached: a workspace holds A + 2 words per packet
+    for (uint64_t done = 0; done < n;) {
+        const uint64_t m = n - done < mmax ? n - done : mmax;
+        const cudaError_t e = G.n_inner > 0 ? heavy_pass<true>(G, cube, pairs + 2 * done, m, W, T, sampled, s)
+                                            : heavy_pass<false>(G, cube, pairs + 2 * done, m, W, T, sampled, s);
+        if (e != cudaSuccess) return e;
+        done += m;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace cbaa

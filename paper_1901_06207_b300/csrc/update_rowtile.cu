@@ -23,6 +23,8 @@
 //                     flush it; then the overflow list, by direct reductions
 // Traffic per packet: 8 B read once (plus 8 B more when every packet is
 // counted), a 4-byte (r >= 5) or 8-byte record written and read once.
+#include <cstring>
+
 #include "cbaa_internal.cuh"
 #include "update_binned.h"
 
@@ -42,6 +44,10 @@ __device__ __forceinline__ uint2 ld_pair(const uint32_t *p) {
 
 __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
     asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_or64(uint32_t *p, uint64_t v) {   // p 8-byte aligned
+    asm volatile("red.global.or.b64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ uint32_t seg_of(const BinSegs &S, uint64_t p) {
@@ -103,11 +109,15 @@ __device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
 constexpr uint32_t kCountTile = 4 * kCountThreads;
 
 // ORIENT (the cube has an inner network): packets are raw {src, dst} (orient()).
+// HASHED: the input is the residual of the heavy split, entries {mangled
+// ip, row} already oriented, one segment of regions of rcap entries whose
+// first rcount[r] are valid (rcap a multiple of every tile and block size).
 // samp > 1: only every samp-th tile of kCountTile packets is counted (a
 // sample for run capacities, see sample_capacity).
-template <bool MULTI, bool ORIENT>
+template <bool MULTI, bool ORIENT, bool HASHED>
 __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
-                                                            uint32_t *__restrict__ counts, uint32_t samp) {
+                                                            uint32_t *__restrict__ counts, uint32_t samp,
+                                                            const uint32_t *__restrict__ rcount, uint64_t rcap) {
     extern __shared__ uint32_t hist[];
     uint64_t lo, hi, step;
     if (MULTI) {
@@ -131,9 +141,15 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
     for (uint32_t i = threadIdx.x; i < B.nbl; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (uint64_t base = lo; base < hi; base += step) {
+        uint64_t thi = hi;                            // end of this tile's valid packets
+        if (HASHED) {
+            const uint64_t r = base / rcap, ve = r * rcap + rcount[r];
+            if (ve < thi) thi = ve;
+            if (base >= thi) continue;
+        }
         const uint32_t s = seg_of(S, base);
         const uint32_t *ptr = S.pairs[s] + 2 * (base - S.start[s]);
-        const bool fast = base + kCountTile <= hi && base + kCountTile <= S.start[s + 1] &&
+        const bool fast = base + kCountTile <= thi && base + kCountTile <= S.start[s + 1] &&
                           (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0;
         if (fast) {
             const uint4 q0 = ld_quad(ptr + 4 * threadIdx.x);
@@ -142,14 +158,22 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
             uint32_t ip[4] = {q0.x, q0.z, q1.x, q1.z}, oip[4] = {q0.y, q0.w, q1.y, q1.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
+                if (HASHED) {
+                    atomicAdd(&hist[rb + row_tile(G, 0, ip[u], oip[u])], 1u);
+                    continue;
+                }
                 if (ORIENT && !orient(G, ip[u], oip[u])) continue;      // raw {src, dst} against NI
                 atomicAdd(&hist[rb + row_tile(G, 0, mangle(G, ip[u]), row_of(G, oip[u]))], 1u);
             }
         } else {
-            const uint64_t end = base + kCountTile < hi ? base + kCountTile : hi;
+            const uint64_t end = base + kCountTile < thi ? base + kCountTile : thi;
             for (uint64_t p = base + threadIdx.x; p < end; p += kCountThreads) {
                 const uint32_t sp = seg_of(S, p);
                 uint2 v = ld_pair(S.pairs[sp] + 2 * (p - S.start[sp]));
+                if (HASHED) {
+                    atomicAdd(&hist[row_tile(G, B.unit(S, sp), v.x, v.y)], 1u);
+                    continue;
+                }
                 if (ORIENT && !orient(G, v.x, v.y)) continue;
                 atomicAdd(&hist[row_tile(G, B.unit(S, sp), mangle(G, v.x), row_of(G, v.y))], 1u);
             }
@@ -163,12 +187,18 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
 // SHORT records (r >= 5): lp << 5 | bit in 4 bytes; else {mangled ip, row}.
 // Shapes of up to 8 packets per thread are held to 32 registers (4-byte
 // records: 2048 threads per SM, measured ~8 % faster) or 42 (8-byte records).
-template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT>
+template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT, bool HASHED>
 __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) / THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                         uint32_t *__restrict__ cursors, void *__restrict__ recs_out,
                                                         const uint32_t *__restrict__ offsets, uint2 *__restrict__ ovf,
-                                                        uint32_t *__restrict__ ovf_count, uint32_t ovf_cap) {
+                                                        uint32_t *__restrict__ ovf_count, uint32_t ovf_cap,
+                                                        const uint32_t *__restrict__ rcount, uint64_t rcap) {
     extern __shared__ uint32_t sm[];
+    if (HASHED) {                                     // the valid part of this block's residual region
+        const uint64_t p0 = (uint64_t)blockIdx.x * THREADS * PPT, r = p0 / rcap, ve = r * rcap + rcount[r];
+        if (ve < n) n = ve;
+        if (p0 >= n) return;
+    }
     uint32_t *hist = sm;
     uint32_t *first = sm + nb;     // exclusive start of each tile's run in `staged`
     uint32_t *delta = sm + 2 * nb;
@@ -222,8 +252,9 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     for (uint32_t k = 0; k < PPT; ++k) {
         slot[k] = 0xFFFFFFFFu;
         if (rt[k] != 0xFFFFFFFFu) {
-            if (ORIENT && !orient(G, rec[k].x, rec[k].y)) continue;      // raw {src, dst} against NI
-            const uint32_t m = mangle(G, rec[k].x), row = row_of(G, rec[k].y);
+            if (!HASHED && ORIENT && !orient(G, rec[k].x, rec[k].y)) continue;      // raw {src, dst} against NI
+            const uint32_t m = HASHED ? rec[k].x : mangle(G, rec[k].x);
+            const uint32_t row = HASHED ? rec[k].y : row_of(G, rec[k].y);
             const uint32_t b = row_tile(G, rt[k], m, row);
             if (SHORT) rec[k].x = ((m >> G.r) << 5) | (row & 31u);
             else rec[k] = make_uint2(m, row);
@@ -352,29 +383,39 @@ __device__ __forceinline__ void overflow_entry(const Geo &G, const BinSegs &S, u
 // more than ch) are taken from a queue, so blocks that drew small tiles take
 // more of them.
 // NRA/NVA > 0 fix the array counts at compile time (the 3+1 layout); 0 reads them from G.
-template <int NRA, int NVA>
+// TEST: read a tile word before its atomic and skip bits already set (where
+// most sets land on set bits: duplicates and heavy sources); else one
+// shared-memory OR per bit (the heavy split's residual: light sources, whose
+// bits are mostly still clear).
+template <bool TEST>
+__device__ __forceinline__ void rt_set(uint32_t *w, uint32_t bit) {
+    if (TEST) tile_set_bit(w, bit);
+    else atomicOr(w, bit);
+}
+
+template <int NRA, int NVA, bool TEST = true>
 __device__ __forceinline__ void rt_apply_lp(const Geo &G, uint32_t *tile, uint32_t lp, uint32_t bit) {
     const uint32_t nra = NRA ? NRA : G.n_ra, nva = NRA ? NVA : G.n_va;
 #pragma unroll
     for (uint32_t i = 0; i < (NRA ? NRA : CBAA_MAX_RA); ++i) {
         if (NRA == 0 && i >= nra) break;
-        tile_set_bit(&tile[tile_off(G, i, ra_col(G, i, lp))], bit);
+        rt_set<TEST>(&tile[tile_off(G, i, ra_col(G, i, lp))], bit);
     }
 #pragma unroll
     for (uint32_t j = 0; j < (NRA ? NVA : CBAA_MAX_ARRAYS); ++j) {
         if (NRA == 0 && j >= nva) break;
-        tile_set_bit(&tile[tile_off(G, nra + j, va_col(G, j, lp))], bit);
+        rt_set<TEST>(&tile[tile_off(G, nra + j, va_col(G, j, lp))], bit);
     }
 }
 
-template <int NRA, int NVA>
+template <int NRA, int NVA, bool TEST = true>
 __device__ __forceinline__ void rt_apply_rec(const Geo &G, uint32_t *tile, uint2 rv) {
-    rt_apply_lp<NRA, NVA>(G, tile, rv.x >> G.r, 1u << (rv.y & 31u));
+    rt_apply_lp<NRA, NVA, TEST>(G, tile, rv.x >> G.r, 1u << (rv.y & 31u));
 }
 
-template <int NRA, int NVA>
+template <int NRA, int NVA, bool TEST = true>
 __device__ __forceinline__ void rt_apply_rec(const Geo &G, uint32_t *tile, uint32_t rv) {
-    rt_apply_lp<NRA, NVA>(G, tile, rv >> 5, 1u << (rv & 31u));
+    rt_apply_lp<NRA, NVA, TEST>(G, tile, rv >> 5, 1u << (rv & 31u));
 }
 
 template <int NRA, int NVA, typename Rec>
@@ -459,6 +500,104 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
     }
 }
 
+// Tiles (cs, 2k) and (cs, 2k + 1) of one cube as one item (item k): both are
+// assembled in shared memory, then each column's two row words, adjacent in
+// the cube (W is even), are ORed in with one 64-bit reduction, which halves
+// the flush's reductions.  For passes whose tiles are of similar size (the
+// heavy split's residual), where whole-pair items balance well.
+template <int NRA, int NVA, typename Rec>
+__global__ void __launch_bounds__(kApplyThreads, 1) k_rt_apply_pair(const Geo G, const BinSegs S,
+                                                                    const Rec *__restrict__ recs,
+                                                                    const uint32_t *__restrict__ offsets,
+                                                                    const uint32_t *__restrict__ cursors,
+                                                                    uint32_t npairs, uint32_t tile_words,
+                                                                    uint32_t *__restrict__ queue,
+                                                                    const uint2 *__restrict__ ovf,
+                                                                    const uint32_t *__restrict__ ovf_count,
+                                                                    uint32_t ovf_cap) {
+    extern __shared__ __align__(16) uint32_t tile[];   // tile 2k, then tile 2k + 1
+    __shared__ uint32_t s_item;
+    uint32_t *t1 = tile + tile_words;
+    const uint4 *a4 = reinterpret_cast<const uint4 *>(tile), *b4 = reinterpret_cast<const uint4 *>(t1);
+    const uint32_t quads = tile_words / 4;                 // arrays start at multiples of 32 words
+    for (uint32_t q = threadIdx.x; q < 2 * quads; q += blockDim.x)
+        reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t k = s_item;
+        if (k >= npairs) break;
+        bool any = false;
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t b = 2 * k + h;
+            // records written: up to the run's end, or fewer when its capacity came from a sample
+            const uint32_t c0 = offsets[b];
+            const uint32_t c1 = offsets[b + 1] < cursors[b] ? offsets[b + 1] : cursors[b];
+            any |= c1 > c0;
+            uint32_t *tl = h ? t1 : tile;
+            uint32_t c = c0 + threadIdx.x;
+            // eight records in flight, the next eight loaded while these are set (one block per
+            // SM leaves registers for it)
+            constexpr uint32_t U = 8;
+            Rec rv[U];
+            bool full = c + (U - 1) * blockDim.x < c1;
+            if (full) {
+#pragma unroll
+                for (uint32_t u = 0; u < U; ++u) rv[u] = __ldcs(recs + c + u * blockDim.x);
+            }
+            while (full) {
+                const uint32_t cn = c + U * blockDim.x;
+                const bool next = cn + (U - 1) * blockDim.x < c1;
+                Rec rn[U];
+                if (next) {
+#pragma unroll
+                    for (uint32_t u = 0; u < U; ++u) rn[u] = __ldcs(recs + cn + u * blockDim.x);
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < U; ++u) rt_apply_rec<NRA, NVA, false>(G, tl, rv[u]);
+#pragma unroll
+                for (uint32_t u = 0; u < U; ++u) rv[u] = rn[u];
+                c = cn;
+                full = next;
+            }
+            for (; c < c1; c += blockDim.x) rt_apply_rec<NRA, NVA, false>(G, tl, __ldcs(recs + c));
+        }
+        __syncthreads();
+        if (!any) continue;                               // the same for every thread
+        const uint32_t cs = (2 * k) / G.W, w = 2 * k - cs * G.W;
+        uint32_t *cube = S.cube[0] + (size_t)cs * G.cs_words + w;
+        for (uint32_t q = threadIdx.x; q < quads; q += blockDim.x) {
+            const uint4 va = a4[q], vb = b4[q];
+            if (!(va.x | va.y | va.z | va.w | vb.x | vb.y | vb.z | vb.w)) continue;
+            const uint32_t t = 4 * q;
+            uint32_t a = 0;                                   // array of tile words t .. t+3
+            while (a + 1 < G.A && t >= G.col_base[a + 1]) ++a;
+            uint32_t *dst = cube + G.arr_base[a] + (size_t)(t - G.col_base[a]) * G.W;
+            const uint32_t lo[4] = {va.x, va.y, va.z, va.w}, hi[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (lo[j] | hi[j]) red_or64(dst + j * G.W, ((uint64_t)hi[j] << 32) | lo[j]);
+            reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
+            reinterpret_cast<uint4 *>(t1)[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+    }
+    // a sampled pass: blocks leaving the item queue take chunks of the overflow list
+    if (!ovf) return;
+    const uint32_t n_ovf = *ovf_count < ovf_cap ? *ovf_count : ovf_cap;
+    constexpr bool SHORT = sizeof(Rec) == 4;
+    for (;;) {
+        __syncthreads();                                  // every thread has read the previous chunk
+        if (threadIdx.x == 0) s_item = atomicAdd(queue + 1, 1u);
+        __syncthreads();
+        const uint64_t c0 = (uint64_t)s_item * blockDim.x;
+        if (c0 >= n_ovf) break;
+        const uint64_t c = c0 + threadIdx.x;
+        if (c < n_ovf) overflow_entry<SHORT>(G, S, ovf[c]);
+    }
+}
+
 // Overflow list of a sampled pass (null: exact counts, no overflow).
 struct Overflow {
     uint2 *list;
@@ -486,48 +625,67 @@ uint32_t routing_table_tiles(const Geo &G, const BinSegs &S, uint32_t nb, uint64
     return span_max * tpr < nb ? (uint32_t)(span_max * tpr) : nb;
 }
 
-template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT>
+template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT, bool HASHED>
 cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
-                              const Overflow &O, cudaStream_t s) {
+                              const Overflow &O, const uint32_t *rcount, uint64_t rcap, cudaStream_t s) {
     // several cubes: every block numbers its own tiles within tables of nbt entries
     const uint32_t nbt = MULTI ? routing_table_tiles(G, S, nb, (uint64_t)THREADS * PPT) : nb;
     const size_t per = SHORT ? 2 : 3;                 // staged record words + bin word per packet
     const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nbt + 1) & ~(size_t)1) + per * THREADS * PPT);
-    cudaError_t e = allow_smem(k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT>, smem);
+    auto k = k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT, HASHED>;
+    cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
-    k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT><<<blocks, THREADS, smem, s>>>(G, S, m, nbt, W.cursors, W.codes,
-                                                                                W.offsets, O.list, O.count, O.cap);
+    k<<<blocks, THREADS, smem, s>>>(G, S, m, nbt, W.cursors, W.codes, W.offsets, O.list, O.count, O.cap, rcount,
+                                    rcap);
     return cudaGetLastError();
 }
 
-template <bool SHORT, bool MULTI, bool ORIENT>
+template <bool SHORT, bool MULTI, bool ORIENT, bool HASHED>
 cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
-                                    const Overflow &O, uint32_t shape, cudaStream_t s) {
+                                    const Overflow &O, uint32_t shape, const uint32_t *rcount, uint64_t rcap,
+                                    cudaStream_t s) {
     switch (shape) {
-        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
-        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
-        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
-        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
-        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
-        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
-        case 7: return launch_rt_scatter<256, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 7: return launch_rt_scatter<256, 16, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
         case 8: {
             // 1024 x 16 stages 16Ki records: with 8-byte records or many tiles it exceeds shared memory
             const uint32_t nbt = MULTI ? routing_table_tiles(G, S, nb, 16384) : nb;
             const size_t need = sizeof(uint32_t) * ((((size_t)3 * nbt + 1) & ~(size_t)1) + (SHORT ? 2 : 3) * 16384);
-            if (need + 1024 > 227u * 1024u) return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
-            return launch_rt_scatter<1024, 16, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+            if (need + 1024 > 227u * 1024u)
+                return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+            return launch_rt_scatter<1024, 16, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
         }
-        default: return launch_rt_scatter<512, 8, SHORT, MULTI, ORIENT>(G, S, m, nb, W, O, s);
+        default: return launch_rt_scatter<512, 8, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
     }
 }
 
 template <bool MULTI, bool ORIENT>
 cudaError_t launch_rt_scatter_kind(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                                    const Overflow &O, uint32_t shape, cudaStream_t s) {
-    return G.r >= 5 ? launch_rt_scatter_shape<true, MULTI, ORIENT>(G, S, m, nb, W, O, shape, s)
-                    : launch_rt_scatter_shape<false, MULTI, ORIENT>(G, S, m, nb, W, O, shape, s);
+    return G.r >= 5 ? launch_rt_scatter_shape<true, MULTI, ORIENT, false>(G, S, m, nb, W, O, shape, nullptr, 1, s)
+                    : launch_rt_scatter_shape<false, MULTI, ORIENT, false>(G, S, m, nb, W, O, shape, nullptr, 1, s);
+}
+
+// Tile pairs fit one block's shared memory.
+bool pair_ok(const Geo &G) { return 2ull * sizeof(uint32_t) * G.col_base[G.A] <= 200u * 1024u; }
+
+template <typename Rec>
+cudaError_t launch_rt_apply_pair(const Geo &G, const BinSegs &S, const BinWs &W, uint32_t nb, uint32_t tw, int sms,
+                                 const uint2 *ovf, const uint32_t *ovf_count, uint32_t ovf_cap, cudaStream_t s) {
+    const bool three_one = G.n_ra == 3 && G.n_va == 1;
+    auto k = three_one ? k_rt_apply_pair<3, 1, Rec> : k_rt_apply_pair<0, 0, Rec>;
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)tw;
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)sms, kApplyThreads, smem, s>>>(G, S, reinterpret_cast<const Rec *>(W.codes), W.offsets, W.cursors,
+                                                 nb / 2, tw, W.nchunk + nb, ovf, ovf_count, ovf_cap);
+    return cudaGetLastError();
 }
 
 template <typename Rec>
@@ -554,7 +712,7 @@ uint32_t rowtile_bins(const Geo &G, uint32_t n_cubes) { return n_cubes * (G.smas
 uint32_t rowtile_words(const Geo &G) { return G.col_base[G.A]; }
 
 constexpr uint32_t kSample = 16;                  // sampled passes count 1 tile in 16
-constexpr uint64_t kMinSampled = 8ull << 20;      // below this every packet is counted
+constexpr uint64_t kMinSampled = kRowTileMinSampled;
 
 // Words of a sampled pass of m packets: records up to the capacity bound,
 // then an overflow list with room for every packet.
@@ -562,9 +720,14 @@ static uint64_t sampled_words(uint64_t m, uint32_t nb, uint64_t rec_words) {
     return ((rec_words * sample_capacity_bound(m, nb, kSample, kCountTile) + 3) & ~3ull) + 2 * m + 8;
 }
 
+uint64_t rowtile_pass_words(const Geo &G, uint64_t m, bool sampled) {
+    const uint64_t rec_words = G.r >= 5 ? 1 : 2;
+    return sampled ? sampled_words(m, rowtile_bins(G, 1), rec_words) : rec_words * m;
+}
+
 // Largest sampled pass (at most `want` packets) that fits the workspace.
-static uint64_t sampled_pass_max(const Geo &G, const BinWs &W, uint32_t nb, uint64_t rec_words, uint64_t want) {
-    const uint64_t cap_words = (uint64_t)W.max_pairs * G.A;
+static uint64_t sampled_pass_max(const BinWs &W, uint32_t nb, uint64_t rec_words, uint64_t want) {
+    const uint64_t cap_words = W.words;
     if (sampled_words(want, nb, rec_words) <= cap_words) return want;
     uint64_t lo = 0, hi = want;
     while (hi - lo > 1) {
@@ -574,36 +737,93 @@ static uint64_t sampled_pass_max(const Geo &G, const BinWs &W, uint32_t nb, uint
     return lo;
 }
 
-cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, const BinWs &W, const cbaa_tuning &T,
-                                  cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    const uint32_t nb = rowtile_bins(G, S0.n_routers);
+// One pass over m packets (HASHED: the residual regions R, m entries at most,
+// the input spans R->nreg * R->rcap positions): counts (or sampled
+// capacities), scan, routing, assembly.
+template <bool MULTI, bool ORIENT, bool HASHED>
+static cudaError_t rowtile_pass(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
+                                const cbaa_tuning &T, bool sampled, const Residual *R, cudaStream_t s) {
     const uint32_t tw = rowtile_words(G);
     const int sms = num_sms();
     const size_t apply_smem = sizeof(uint32_t) * tw;
-    cudaError_t e;
-    const bool multi = S0.n_routers > 1, ori = G.n_inner > 0;
-    auto kcount = multi ? (ori ? k_rt_count<true, true> : k_rt_count<true, false>)
-                        : (ori ? k_rt_count<false, true> : k_rt_count<false, false>);
-    if ((e = allow_smem(kcount, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
     const bool short_rec = G.r >= 5;                  // lp (32 - r bits) and the bit fit one word
     const uint64_t rec_words = short_rec ? 1 : 2;
     const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
     const uint32_t apply_ips = T.apply_items_per_sm ? T.apply_items_per_sm : 8;
-    const uint64_t max_pairs = W.max_pairs * G.A / rec_words;   // the buffer holds A words per packet
+    const uint32_t samp = sampled ? kSample : 1u;
+    auto kcount = k_rt_count<MULTI, ORIENT, HASHED>;
+    cudaError_t e;
+    if ((e = allow_smem(kcount, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
+    // counts[nb] is the overflow counter of a sampled pass (a residual pass finds them zeroed by the split)
+    if (!HASHED && (e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * (nb + 1), s)) != cudaSuccess) return e;
+    const uint64_t span = HASHED ? (uint64_t)R->nreg * R->rcap : m;      // positions the kernels walk
+    const uint32_t *rcount = HASHED ? R->rcount : nullptr;
+    const uint64_t rcap = HASHED ? R->rcap : 1;
+    const uint64_t want = (span + (uint64_t)kCountTile * samp - 1) / ((uint64_t)kCountTile * samp);
+    const uint64_t cap = (uint64_t)sms * count_bps;
+    const unsigned cgrid = (unsigned)(want < cap ? want : cap);
+    // split a row tile only when it holds more than apply_ips/2 times the average tile
+    uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
+    if (ch < (1u << 12)) ch = 1u << 12;
+    kcount<<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, span, nb, W.counts, samp, rcount, rcap);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s, samp)) != cudaSuccess) return e;
+    Overflow O{nullptr, nullptr, 0};
+    if (sampled) {
+        const uint64_t rec_region = (rec_words * sample_capacity_bound(m, nb, kSample, kCountTile) + 3) & ~3ull;
+        O = Overflow{reinterpret_cast<uint2 *>(W.codes + rec_region), W.counts + nb, (uint32_t)m};
+    }
+    if (HASHED)
+        e = short_rec ? launch_rt_scatter_shape<true, false, false, true>(G, S, span, nb, W, O, T.scatter_shape, rcount,
+                                                                          rcap, s)
+                      : launch_rt_scatter_shape<false, false, false, true>(G, S, span, nb, W, O, T.scatter_shape,
+                                                                           rcount, rcap, s);
+    else
+        e = launch_rt_scatter_kind<MULTI, ORIENT>(G, S, m, nb, W, O, T.scatter_shape, s);
+    if (e != cudaSuccess) return e;
+    if (HASHED && pair_ok(G))                         // residual tiles are of similar size: whole pairs
+        return short_rec ? launch_rt_apply_pair<uint32_t>(G, S, W, nb, tw, sms, O.list, O.count, O.cap, s)
+                         : launch_rt_apply_pair<uint2>(G, S, W, nb, tw, sms, O.list, O.count, O.cap, s);
+    return short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, O.list, O.count,
+                                                 O.cap, s)
+                     : launch_rt_apply<uint2>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, O.list, O.count, O.cap,
+                                              s);
+}
+
+cudaError_t rowtile_pass_hashed(const Geo &G, uint32_t *cube, const Residual &R, uint64_t m, const BinWs &W,
+                                const cbaa_tuning &T, bool sampled, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    BinSegs S;
+    memset(&S, 0, sizeof S);
+    S.pairs[0] = reinterpret_cast<const uint32_t *>(R.entries);
+    S.start[0] = 0;
+    S.start[1] = (uint64_t)R.nreg * R.rcap;
+    S.router[0] = 0;
+    S.cube[0] = cube;
+    S.k = 1;
+    S.n_routers = 1;
+    return rowtile_pass<false, false, true>(G, S, m, rowtile_bins(G, 1), W, T, sampled, &R, s);
+}
+
+cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, const BinWs &W, const cbaa_tuning &T,
+                                  cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t nb = rowtile_bins(G, S0.n_routers);
+    const bool multi = S0.n_routers > 1, ori = G.n_inner > 0;
+    const uint64_t rec_words = G.r >= 5 ? 1 : 2;
+    const uint64_t max_pairs = W.words / rec_words;            // counted passes: one record per packet
     // tile_kind 3: run capacities from a 1-in-16 sample of the packets (records
     // past a capacity take the overflow path), where the workspace allows it
     // tile_kind 0 (the default) samples passes of at least kMinSampled packets
     uint64_t max_sampled = 0;
     if (T.tile_kind == 3 || (T.tile_kind == 0 && n >= kMinSampled)) {
-        max_sampled = sampled_pass_max(G, W, nb, rec_words, n);
+        max_sampled = sampled_pass_max(W, nb, rec_words, n);
         // kind 3: any pass of a useful size; kind 0: only where it takes no more passes than counting
         const uint64_t counted = n < max_pairs ? n : max_pairs;
         const uint64_t least = T.tile_kind == 3 ? (n < (1u << 16) ? n : (1u << 16)) : counted;
         if (max_sampled < least) max_sampled = 0;
     }
     const bool sampled = max_sampled > 0;
-    const uint32_t samp = sampled ? kSample : 1u;
     for (uint64_t done = 0; done < n;) {
         const uint64_t lim = sampled ? max_sampled : max_pairs;
         const uint64_t m = (n - done) < lim ? (n - done) : lim;
@@ -619,33 +839,13 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S0, uint64_t n, c
             ++S.k;
         }
         S.start[S.k] = m;
-        // counts[nb] is the overflow counter of a sampled pass
-        if ((e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * (nb + 1), s)) != cudaSuccess) return e;
-        const uint64_t want = (m + (uint64_t)kCountTile * samp - 1) / ((uint64_t)kCountTile * samp);
-        const uint64_t cap = (uint64_t)sms * count_bps;
-        const unsigned cgrid = (unsigned)(want < cap ? want : cap);
-        // split a row tile only when it holds more than apply_ips/2 times the average tile
-        uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
-        if (ch < (1u << 12)) ch = 1u << 12;
-        kcount<<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, m, nb, W.counts, samp);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s, samp)) != cudaSuccess) return e;
-        Overflow O{nullptr, nullptr, 0};
-        if (sampled) {
-            const uint64_t rec_region = (rec_words * sample_capacity_bound(m, nb, kSample, kCountTile) + 3) & ~3ull;
-            O = Overflow{reinterpret_cast<uint2 *>(W.codes + rec_region), W.counts + nb, (uint32_t)m};
-        }
+        cudaError_t e;
         if (multi)
-            e = ori ? launch_rt_scatter_kind<true, true>(G, S, m, nb, W, O, T.scatter_shape, s)
-                    : launch_rt_scatter_kind<true, false>(G, S, m, nb, W, O, T.scatter_shape, s);
+            e = ori ? rowtile_pass<true, true, false>(G, S, m, nb, W, T, sampled, nullptr, s)
+                    : rowtile_pass<true, false, false>(G, S, m, nb, W, T, sampled, nullptr, s);
         else
-            e = ori ? launch_rt_scatter_kind<false, true>(G, S, m, nb, W, O, T.scatter_shape, s)
-                    : launch_rt_scatter_kind<false, false>(G, S, m, nb, W, O, T.scatter_shape, s);
-        if (e != cudaSuccess) return e;
-        e = short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, O.list, O.count,
-                                                  O.cap, s)
-                      : launch_rt_apply<uint2>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, O.list, O.count, O.cap,
-                                               s);
+            e = ori ? rowtile_pass<false, true, false>(G, S, m, nb, W, T, sampled, nullptr, s)
+                    : rowtile_pass<false, false, false>(G, S, m, nb, W, T, sampled, nullptr, s);
         if (e != cudaSuccess) return e;
         done += m;
     }

@@ -103,7 +103,9 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
 
 def test_update_workspace_limits(C):
     """The partitioned update covers cubes up to 512 MiB; larger ones get no workspace size."""
-    assert C.update_workspace_bytes(GEO.L2, 1 << 20) >= (1 << 20) * 4 * 4
+    # A + 2 words per packet: A codes (column tiles), or a residual entry of the heavy split plus a
+    # record and an overflow entry (row tiles)
+    assert C.update_workspace_bytes(GEO.L2, 1 << 20) >= (1 << 20) * 4 * 6
     assert C.update_workspace_bytes(GEO.SERVE, 1) > 0
     big = C.make_params(8, 3, 1, 10, [13])          # 1 GiB cube
     assert C.validate(big) == C.OK and C.update_workspace_bytes(big, 1024) == 0
@@ -113,11 +115,13 @@ def test_update_workspace_limits(C):
 def test_tuning_roundtrip_and_limits(C):
     before = C.get_tuning()
     C.set_tuning(scatter_shape=3, count_blocks_per_sm=4, apply_items_per_sm=16, direct_blocks_per_sm=2,
-                 tile_kind=1)
+                 tile_kind=1, heavy=2)
     assert C.get_tuning() == dict(scatter_shape=3, count_blocks_per_sm=4, apply_items_per_sm=16,
-                                  direct_blocks_per_sm=2, tile_kind=1)
+                                  direct_blocks_per_sm=2, tile_kind=1, heavy=2)
     with pytest.raises(C.CbaaError):
         C.set_tuning(tile_kind=4)
+    with pytest.raises(C.CbaaError):
+        C.set_tuning(heavy=4)
     with pytest.raises(C.CbaaError):
         C.set_tuning(scatter_shape=9)
     C.set_tuning(**before)
