@@ -894,8 +894,9 @@ def run_batched(args):
                        "windows": len(wins), "routers": R, "packets_per_window": n_per[0],
                        "router_loads": "lognormal(sigma=0.8) weights over a 5-tuple hash",
                        "geometry": "r=5, |RA|=3, |VA|=1, g=2^10, c=2^12 (64 MiB per cube)", "theta": theta,
-                       "step": "one CUDA graph replay: per window reset router cubes, one partitioned update "
-                               "pass over all routers, global cube w mod 2 = OR of the router cubes, detect on a "
+                       "step": "one CUDA graph replay: per window reset the router cubes and global cube w mod 2, "
+                               "one partitioned update pass over all routers that also ORs every word it flushes "
+                               "into the global cube (the merge of Section III.C in the same pass), detect on a "
                                "side stream (overlapping the next window's router update)",
                        "l2": "inputs larger than L2 (2 GiB of packets per step)"},
             "window_ms": ms / steps / len(wins), "router_update_tiling": tiling,

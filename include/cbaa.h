@@ -225,6 +225,16 @@ size_t cbaa_update_multi_workspace_bytes(const cbaa_params *p, int n_cubes, size
 int cbaa_cube_update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs, const size_t *n,
                            void *dev_ws, size_t ws_bytes, void *stream);
 
+/* cbaa_cube_update_multi plus the global server's merge of Section III.C in
+ * the same pass, async: every word the pass ORs into a router cube is ORed
+ * into `global` too, so global |= the bits this pass sets in any router
+ * cube (global = OR of the router cubes when they and global start empty),
+ * with no separate merge pass reading the router cubes back.  global: same
+ * geometry as the cubes (else CBAA_ERR_GEOMETRY), not one of them (else
+ * CBAA_ERR_INVALID_ARG); same workspace as cbaa_cube_update_multi. */
+int cbaa_cube_update_multi_merge(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs,
+                                 const size_t *n, cbaa_cube *global, void *dev_ws, size_t ws_bytes, void *stream);
+
 /* Set / read the process-wide launch shapes of the update kernels (for an
  * autotuner).  Results never depend on them.  Not synchronised with calls
  * running on other host threads: set them before launching work. */

@@ -5,9 +5,10 @@ local cube (Alg. 1); at the end of each time window the global server ORs
 the local cubes together and restores the super hosts (Alg. 2, Alg. 3).
 Here the routers are local cubes on one GPU.  For each window the
 library's partitioned update feeds all router cubes in one pass (so uneven
-router loads share the whole GPU), the router cubes are OR-merged into the
-global cube, and the detect writes that window's host list to device
-memory.  The global cube is double-buffered: window w's detect runs on a
+router loads share the whole GPU) and ORs every word it flushes into a
+router cube into the global cube as well (the global server's merge,
+without a second pass over the router cubes), and the detect writes that
+window's host list to device memory.  The global cube is double-buffered: window w's detect runs on a
 side stream while window w+1's routers are reset and updated, as a global
 server detects one window while the routers scan the next.  A sequence of
 windows is recorded once into a CUDA graph (a fork/join over the two
@@ -45,18 +46,19 @@ class RouterWindows:
     _last_w = None
 
     def enqueue_window(self, w: int, router_pairs, done=None):
-        """One window on the current stream: reset router cubes, one update pass over all of them,
-        global cube w mod 2 = OR of the router cubes; its detect goes to the side stream.  `done[b]` is
-        the event after the last detect of global cube b (reset waits for it)."""
+        """One window on the current stream: reset router cubes and global cube w mod 2, one update
+        pass over all router cubes that also ORs every bit it sets into the global cube (so global = OR
+        of the router cubes without a merge pass reading them back); the detect goes to the side
+        stream.  `done[b]` is the event after the last detect of global cube b (its reset waits)."""
         torch = C._torch()
         main = torch.cuda.current_stream()
         b = w & 1
         for c in self.routers:
             c.reset()
-        C.update_multi(self.routers, router_pairs, self.uws)
         if done is not None and done[b] is not None:
             main.wait_event(done[b])
-        self.globs[b].merge(self.routers, assign=True)      # global = OR of the router cubes
+        self.globs[b].reset()
+        C.update_multi(self.routers, router_pairs, self.uws, merge_into=self.globs[b])
         merged = torch.cuda.Event()
         merged.record(main)
         self.side.wait_event(merged)
@@ -94,9 +96,10 @@ class RouterWindows:
                 for rep in range(reps + 1):
                     for c in self.routers:
                         c.reset()
+                    self.globs[0].reset()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    C.update_multi(self.routers, windows[0], self.uws)
+                    C.update_multi(self.routers, windows[0], self.uws, merge_into=self.globs[0])
                     e1.record(stream)
                     torch.cuda.synchronize()
                     if rep:

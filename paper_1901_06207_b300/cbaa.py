@@ -101,6 +101,8 @@ def _signatures():
         "cbaa_update_multi_workspace_bytes": (sz, [P, ctypes.c_int, sz]),
         "cbaa_cube_update_multi": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                                   ctypes.POINTER(sz), vp, sz, vp]),
+        "cbaa_cube_update_multi_merge": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                                        ctypes.POINTER(sz), vp, vp, sz, vp]),
         "cbaa_set_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
         "cbaa_host_features": (ctypes.c_int, [vp, vp, vp, vp, sz, vp, vp]),
         "cbaa_mlp_forward": (ctypes.c_int, [vp, vp, sz, vp, vp]),
@@ -234,14 +236,19 @@ def get_tuning() -> dict:
     return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
 
-def update_multi(cubes, pairs_list, ws: "UpdateWorkspace", counts=None, stream=None):
-    """Alg. 1 for several router cubes in one partitioned pass: pairs_list[j] feeds cubes[j]."""
+def update_multi(cubes, pairs_list, ws: "UpdateWorkspace", counts=None, stream=None, merge_into=None):
+    """Alg. 1 for several router cubes in one partitioned pass: pairs_list[j] feeds cubes[j].  With
+    ``merge_into`` (a Cube), every bit the pass sets is ORed into it as well (the global merge)."""
     k = len(cubes)
     hs = (ctypes.c_void_p * k)(*[c.handle.value for c in cubes])
     ps = (ctypes.c_void_p * k)(*[p.data_ptr() if p is not None and p.numel() else None for p in pairs_list])
     if counts is None:
         counts = [0 if p is None else (p.shape[0] if p.dim() == 2 else p.numel() // 2) for p in pairs_list]
     ns = (ctypes.c_size_t * k)(*counts)
+    if merge_into is not None:
+        _check(lib().cbaa_cube_update_multi_merge(hs, k, ps, ns, merge_into.handle, ws.ptr, ws.nbytes,
+                                                  _stream_ptr(stream)), "cube_update_multi_merge")
+        return
     _check(lib().cbaa_cube_update_multi(hs, k, ps, ns, ws.ptr, ws.nbytes, _stream_ptr(stream)), "cube_update_multi")
 
 

@@ -215,8 +215,13 @@ size_t cbaa_update_multi_workspace_bytes(const cbaa_params *p, int n_cubes, size
     return cbaa::bin_ws_bytes(G, (uint32_t)n_cubes, max_pairs);
 }
 
-int cbaa_cube_update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs, const size_t *n,
-                           void *dev_ws, size_t ws_bytes, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// cbaa_cube_update_multi, and with `global` set cbaa_cube_update_multi_merge.
+int update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs, const size_t *n,
+                 cbaa_cube *global, void *dev_ws, size_t ws_bytes, void *stream) {
     if (!cubes || !dev_pairs || !n || n_cubes < 1 || n_cubes > (int)cbaa::kMaxRouters) return CBAA_ERR_INVALID_ARG;
     if (!dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u)) return CBAA_ERR_INVALID_ARG;
     const cbaa_cube *c0 = cubes[0];
@@ -250,10 +255,31 @@ int cbaa_cube_update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t 
         total += n[j];
     }
     S.start[S.k] = total;
+    if (global) {                                    // the global cube: same structure, not a router cube
+        if (std::memcmp(&global->p, &c0->p, sizeof(cbaa_params)) != 0) return CBAA_ERR_GEOMETRY;
+        for (int j = 0; j < n_cubes; ++j)
+            if (cubes[j] == global) return CBAA_ERR_INVALID_ARG;
+        S.merge = global->data;
+    }
     if (total == 0) return CBAA_OK;
     cbaa::BinWs W;
     if (!cbaa::bin_ws_make(G, (uint32_t)n_cubes, dev_ws, ws_bytes, &W)) return CBAA_ERR_INVALID_ARG;
     return cuda_status(cbaa::launch_update_segments(G, S, total, W, current_tuning(), as_stream(stream)));
+}
+
+}  // namespace
+
+extern "C" {
+
+int cbaa_cube_update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs, const size_t *n,
+                           void *dev_ws, size_t ws_bytes, void *stream) {
+    return update_multi(cubes, n_cubes, dev_pairs, n, nullptr, dev_ws, ws_bytes, stream);
+}
+
+int cbaa_cube_update_multi_merge(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs,
+                                 const size_t *n, cbaa_cube *global, void *dev_ws, size_t ws_bytes, void *stream) {
+    if (!global) return CBAA_ERR_INVALID_ARG;
+    return update_multi(cubes, n_cubes, dev_pairs, n, global, dev_ws, ws_bytes, stream);
 }
 
 int cbaa_cube_update_binned(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *dev_ws, size_t ws_bytes,

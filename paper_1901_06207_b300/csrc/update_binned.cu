@@ -289,7 +289,10 @@ __global__ void __launch_bounds__(kApplyThreads) k_bin_apply(const BinSegs S, ui
         uint32_t *dst = S.cube[r] + base;
         for (uint32_t w = threadIdx.x; w < lim; w += blockDim.x) {
             const uint32_t v = tile[w];
-            if (v) red_or(dst + w, v);
+            if (v) {
+                red_or(dst + w, v);
+                if (S.merge) red_or(S.merge + base + w, v);     // the global server's OR, in the same pass
+            }
         }
         __syncthreads();
     }
@@ -378,7 +381,7 @@ cudaError_t launch_bin_scan(uint32_t *counts, uint32_t nb, uint32_t ch, const Bi
 cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    if (S.k == 1 && heavy_enabled(G, S.n_routers, n, T))
+    if (S.k == 1 && !S.merge && heavy_enabled(G, S.n_routers, n, T))
         return launch_update_heavy(G, S.cube[S.router[0]], S.pairs[0], n, W, T, s);
     if (T.tile_kind != 1 && rowtile_ok(G, S.n_routers)) return launch_update_rowtile(G, S, n, W, T, s);
     if (G.n_ra == 3 && G.n_va == 1) return launch_binned_t<3, 1>(G, S, n, W, T, s);

@@ -25,6 +25,7 @@ struct BinSegs {
     uint64_t start[kMaxSegs + 1];
     uint32_t router[kMaxSegs];
     uint32_t *cube[kMaxRouters];
+    uint32_t *merge;          // or null: every word ORed into a cube is ORed here too (the global cube)
     uint32_t k;               // segments
     uint32_t n_routers;       // cubes
     uint32_t tiles_per_seg;   // tiles per cube

@@ -14,8 +14,8 @@
 //                       address seen in each slot)
 //   2. k_heavy_hist, k_heavy_select : the most counted slots, up to K of
 //                       them, become the heavy sources; a lookup table maps a
-//                       mangled address to its heavy index (top 13 bits ->
-//                       low 19 bits as a tag and the index)
+//                       mangled address to its heavy index (top 14 bits ->
+//                       low 18 bits as a tag and the index)
 //   3. k_heavy_split  : every packet: a heavy source's row bit is set in
 //                       its bitmap in shared memory (a bit already set is
 //                       only read); any other packet is written out as
@@ -61,8 +61,8 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
 }
 
 // Heavy index of mangled address m, or kHeavyIdxMask.  d = entry ^ (tag of
-// m << 13) keeps only the index field exactly when the tags agree, and the
-// empty marker's index field is all ones.
+// m << kHeavyTabBits) keeps only the index field exactly when the tags agree,
+// and the empty marker's index field is all ones.
 __device__ __forceinline__ uint32_t heavy_index(const uint32_t *tab, uint32_t m) {
     const uint32_t d = tab[m >> kHeavyTagBits] ^ ((m & kTagMask) << kHeavyTabBits);
     return d < kHeavyIdxMask ? d : kHeavyIdxMask;

@@ -372,10 +372,12 @@ __device__ __forceinline__ void overflow_entry(const Geo &G, const BinSegs &S, u
         w = row >> 5;
         bit = row & 31u;
     }
-    uint32_t *base = S.cube[router] + (size_t)cs * G.cs_words + w;
+    const size_t off = (size_t)cs * G.cs_words + w;
     for (uint32_t a = 0; a < G.A; ++a) {
         const uint32_t col = a < G.n_ra ? ra_col(G, a, lp) : va_col(G, a - G.n_ra, lp);
-        red_or(base + G.arr_base[a] + (size_t)col * G.W, 1u << bit);
+        const size_t o = off + G.arr_base[a] + (size_t)col * G.W;
+        red_or(S.cube[router] + o, 1u << bit);
+        if (S.merge) red_or(S.merge + o, 1u << bit);
     }
 }
 
@@ -481,6 +483,13 @@ __global__ void __launch_bounds__(kApplyThreads) k_rt_apply(const Geo G, const B
             if (v.y) red_or(dst + G.W, v.y);
             if (v.z) red_or(dst + 2 * G.W, v.z);
             if (v.w) red_or(dst + 3 * G.W, v.w);
+            if (S.merge) {                                    // the global server's OR, in the same pass
+                uint32_t *mdst = S.merge + (dst - S.cube[router]);
+                if (v.x) red_or(mdst, v.x);
+                if (v.y) red_or(mdst + G.W, v.y);
+                if (v.z) red_or(mdst + 2 * G.W, v.z);
+                if (v.w) red_or(mdst + 3 * G.W, v.w);
+            }
             tile4[q] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();

@@ -150,6 +150,47 @@ def _multi_router_case(C, oracle, geo, win, k):
     assert np.array_equal(glob.to_numpy(), oracle.build_cube(d, w.pairs))
 
 
+@pytest.mark.parametrize("kind", [1, 2, 3])
+@pytest.mark.parametrize("geo,win,k", [("TINY2", "tiny", 5), ("L2", "4m", 8)])
+def test_multi_router_update_merges_into_global(C, oracle, geo, win, k, kind):
+    """cbaa_cube_update_multi_merge: each router cube is the oracle cube of its own packets, and the
+    global cube -- holding earlier bits of its own -- gains exactly the OR of all router cubes (the
+    merge of Section III.C done in the update pass); a small workspace forces several passes."""
+    import torch
+    d = GEO.ALL[geo]
+    w = window(win)
+    rid, _ = T.split_by_router(w.pairs, 93, k)
+    parts = [w.pairs[rid == j] for j in range(k)]
+    earlier = tiny_window(77, n=1 << 14).pairs
+    before = C.get_tuning()
+    try:
+        C.set_tuning(**{**before, "tile_kind": kind})
+        cubes = [C.Cube(d) for _ in range(k)]
+        glob = C.Cube(d)
+        glob.update(dev_pairs(earlier))
+        ws = C.UpdateWorkspace(d, max(1, w.pairs.shape[0] // 3), n_cubes=k)
+        C.update_multi(cubes, [dev_pairs(p) if p.size else None for p in parts], ws, merge_into=glob)
+        torch.cuda.synchronize()
+    finally:
+        C.set_tuning(**before)
+    for j in range(k):
+        assert np.array_equal(cubes[j].to_numpy(), oracle.build_cube(d, parts[j])), j
+    assert np.array_equal(glob.to_numpy(), oracle.build_cube(d, np.concatenate([earlier, w.pairs])))
+
+
+def test_multi_merge_rejects_bad_global(C):
+    d = GEO.TINY
+    cubes = [C.Cube(d) for _ in range(2)]
+    pairs = [dev_pairs(tiny_window(78, n=1 << 10).pairs), None]
+    ws = C.UpdateWorkspace(d, 1 << 10, n_cubes=2)
+    with pytest.raises(C.CbaaError) as e:
+        C.update_multi(cubes, pairs, ws, merge_into=cubes[1])            # a router cube itself
+    assert e.value.status == C.ERR_INVALID_ARG
+    with pytest.raises(C.CbaaError) as e:
+        C.update_multi(cubes, pairs, ws, merge_into=C.Cube(GEO.TINY2))   # another structure
+    assert e.value.status == C.ERR_GEOMETRY
+
+
 @pytest.mark.parametrize("shape", [0, 6])
 @pytest.mark.parametrize("kind", [2, 3])
 def test_multi_router_segment_edges(C, oracle, shape, kind):
