@@ -314,6 +314,86 @@ cudaError_t launch_merge(uint32_t *dst, const uint32_t *const *srcs, int k, uint
     return cudaSuccess;
 }
 
+// Zero counts for columns of at most 16 pieces of 16 bytes (g <= 2048):
+// TPC = W/4 lanes share a column, one piece each, so a warp's load covers
+// 32/TPC whole columns, 512 contiguous bytes (full 128-byte lines: four L1
+// wavefronts, where pieces strided over sixteen columns take sixteen).  Each
+// lane keeps U = max(8, TPC) loads in flight, then a butterfly over the TPC lanes of a
+// column (log2 TPC exchange steps, U/2 + U/4 + ... shuffles) leaves each lane
+// the totals of U/TPC columns: value i of lane l is load u = i + (U/TPC)(l mod
+// TPC), column group l/TPC of that load.
+template <uint32_t TPC>
+__global__ void __launch_bounds__(256) k_zero_counts_lines(const Geo G, const uint32_t *__restrict__ cube,
+                                                           uint16_t *__restrict__ zc,
+                                                           unsigned long long *__restrict__ za, uint32_t splits,
+                                                           uint32_t arr0, uint32_t *__restrict__ done, double E,
+                                                           double *__restrict__ eps_out,
+                                                           int64_t *__restrict__ zmax_out, uint32_t cs_lo,
+                                                           uint32_t cs_hi) {
+    constexpr uint32_t U = TPC > 8 ? TPC : 8;        // loads in flight (at least the lanes of a column)
+    constexpr uint32_t CPL = 32 / TPC;               // columns per warp load
+    const uint32_t arr = arr0 + blockIdx.x;          // cs*A + a
+    const uint32_t cs = arr / G.A, a = arr % G.A;
+    const uint32_t ncol = 1u << G.cbn[a];
+    const uint32_t c0 = (uint32_t)(((uint64_t)ncol * blockIdx.y) / splits);
+    const uint32_t c1 = (uint32_t)(((uint64_t)ncol * (blockIdx.y + 1)) / splits);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint4 *arr4 = reinterpret_cast<const uint4 *>(cube + (size_t)cs * G.cs_words + G.arr_base[a]);
+    unsigned long long acc = 0;
+    for (uint32_t base = c0 + warp * U * CPL; base < c1; base += nwarps * U * CPL) {
+        uint32_t x[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) {
+            const uint32_t col = base + u * CPL + lane / TPC;
+            x[u] = 0;
+            if (col < c1) {
+                const uint4 v = __ldcg(arr4 + (size_t)col * TPC + (lane % TPC));
+                x[u] = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+        }
+#pragma unroll
+        for (uint32_t o = TPC / 2, V = U; o > 0; o >>= 1, V >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (uint32_t i = 0; i < V / 2; ++i) {
+                const uint32_t send = up ? x[i] : x[i + V / 2];
+                const uint32_t keep = up ? x[i + V / 2] : x[i];
+                x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < U / TPC; ++i) {
+            const uint32_t u = i + (U / TPC) * (lane % TPC);
+            const uint32_t col = base + u * CPL + lane / TPC;
+            if (col < c1) {
+                const uint32_t zeros = G.g - x[i];
+                if (zc) zc[(size_t)arr * G.cmax + col] = (uint16_t)zeros;
+                acc += zeros;
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    __shared__ unsigned long long part[8];
+    if (lane == 0) part[warp] = acc;
+    __syncthreads();
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (uint32_t w = 0; w < nwarps; ++w) t += part[w];
+        atomicAdd(&za[arr], t);
+        s_last = false;
+        if (done) {
+            __threadfence();
+            s_last = atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1;
+        }
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (uint32_t c = cs_lo + threadIdx.x; c < cs_hi; c += blockDim.x) eps_zmax_of(G, za, E, c, eps_out, zmax_out);
+    }
+}
+
 cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc, uint64_t *za,
                                 double *eps, int64_t *zmax, double E, cudaStream_t s, uint32_t cs_lo,
                                 uint32_t cs_hi, uint32_t *done, bool za_zeroed) {
@@ -329,9 +409,33 @@ cudaError_t launch_column_stats(const Geo &G, const uint32_t *cube, uint16_t *zc
     const uint32_t min_cols = 1u << 5;   // cbn >= 5 for every array
     if (splits > min_cols) splits = min_cols;
     const bool fused = done && (eps || zmax);
-    k_zero_counts<<<dim3(arrays, splits), 256, 0, s>>>(G, cube, zc, reinterpret_cast<unsigned long long *>(za), splits,
-                                                       cs_lo * G.A, fused ? done : nullptr, E, eps, zmax, cs_lo,
-                                                       cs_hi);
+    auto *zap = reinterpret_cast<unsigned long long *>(za);
+    uint32_t *dn = fused ? done : nullptr;
+    const uint32_t pieces = G.W / 4;                 // 16-byte pieces per column
+    if (pieces <= 16) {
+        // whole lines per warp load; a slice per block of at least one pass of its 8 warps x U loads
+        const uint32_t per_pass = 8 * (pieces > 8 ? pieces : 8) * (32 / pieces);
+        // about two blocks per SM, each looping over its slice: fewer block ends (a fence and a shared
+        // counter atomic each) and the next pass's loads issued while others reduce
+        uint32_t sl = 1;
+        while ((uint64_t)arrays * sl < (uint64_t)num_sms() * 2 && sl < splits && G.cmax / (2 * sl) >= per_pass)
+            sl <<= 1;
+        switch (pieces) {
+            case 1: k_zero_counts_lines<1><<<dim3(arrays, sl), 256, 0, s>>>(G, cube, zc, zap, sl, cs_lo * G.A, dn, E,
+                                                                            eps, zmax, cs_lo, cs_hi); break;
+            case 2: k_zero_counts_lines<2><<<dim3(arrays, sl), 256, 0, s>>>(G, cube, zc, zap, sl, cs_lo * G.A, dn, E,
+                                                                            eps, zmax, cs_lo, cs_hi); break;
+            case 4: k_zero_counts_lines<4><<<dim3(arrays, sl), 256, 0, s>>>(G, cube, zc, zap, sl, cs_lo * G.A, dn, E,
+                                                                            eps, zmax, cs_lo, cs_hi); break;
+            case 8: k_zero_counts_lines<8><<<dim3(arrays, sl), 256, 0, s>>>(G, cube, zc, zap, sl, cs_lo * G.A, dn, E,
+                                                                            eps, zmax, cs_lo, cs_hi); break;
+            default: k_zero_counts_lines<16><<<dim3(arrays, sl), 256, 0, s>>>(G, cube, zc, zap, sl, cs_lo * G.A, dn,
+                                                                              E, eps, zmax, cs_lo, cs_hi); break;
+        }
+    } else {
+        k_zero_counts<<<dim3(arrays, splits), 256, 0, s>>>(G, cube, zc, zap, splits, cs_lo * G.A, dn, E, eps, zmax,
+                                                           cs_lo, cs_hi);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((eps || zmax) && !fused) {

@@ -411,6 +411,28 @@ def test_column_stats_bit_exact(C, oracle, geo, win, theta, form):
         assert st["zmax"][cs] == oracle.zmax(d, e, E)
 
 
+@pytest.mark.parametrize("log2_g,cbn", [(8, [9, 9, 10, 8]), (9, [10, 10, 10, 9]), (11, [9, 9, 9, 9])])
+def test_column_stats_every_column_length(C, oracle, log2_g, cbn):
+    """Columns of 2, 4 and 16 pieces of 16 bytes (g = 2^8, 2^9, 2^11; the 1- and 8-piece cases and the
+    long columns are in the test above), with unequal array widths: zero counts, array totals, eps and
+    Zmax against the oracle."""
+    d = C.make_params(6, 3, 1, log2_g, cbn)
+    w = window("tiny")
+    cube = C.Cube(d)
+    cube.update(dev_pairs(w.pairs))
+    st = cube.column_stats(128)
+    host = oracle.build_cube(d, w.pairs)
+    zc, za = oracle.zero_counts(d, host)
+    for a in range(4):
+        c = 1 << d["cbn"][a]
+        assert np.array_equal(st["zc"][:, a, :c].astype(np.uint32), zc[:, a, :c])
+    assert np.array_equal(st["za"], za)
+    E = oracle.exp_factor(128, log2_g)
+    for cs in range(1 << d["r"]):
+        e = oracle.eps(d, za, cs)
+        assert st["eps"][cs] == e and st["zmax"][cs] == oracle.zmax(d, e, E)
+
+
 DETECT_CASES = [("TINY", "tiny", 128, 0), ("TINY", "tiny", 96, 1), ("TINY", "tiny_sat", 128, 0),
                 ("TINY2", "tiny", 128, 0), ("PAPER", "1m", 1024, 0), ("PAPER", "1m", 1024, 1),
                 ("L2", "4m", 1024, 0), ("L2", "4m", 700, 1), ("UNDERSIZED", "4m", 1024, 0),
