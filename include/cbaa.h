@@ -376,6 +376,13 @@ int cbaa_mlp_adam(float *dev_master, const float *dev_grad, float *dev_m, float 
 /* dev_w_bf16 = round-to-nearest-even BF16 of dev_master; async. */
 int cbaa_mlp_to_bf16(const float *dev_master, uint16_t *dev_w_bf16, void *stream);
 
+/* Training target per sample, async: dev_t[s] = ln(1 + dev_count[s]) -
+ * ln(1 + est_s), the correction the network learns, with est_s the Thm. 2
+ * estimate carried in the features (dev_feats float[n][16] from
+ * cbaa_host_features) and dev_count the exact cardinality (the baseline of
+ * Section V.A, 0 for an address never seen).  dev_count, dev_t float[n]. */
+int cbaa_learned_target(const float *dev_feats, const float *dev_count, size_t n, float *dev_t, void *stream);
+
 /* Super-host decision per address, async: card = exp(ln(1 + est) + y) - 1
  * with est the Thm. 2 estimate carried in the features, or est itself when
  * y is not finite; decision = card >= theta.  dev_card float[n],

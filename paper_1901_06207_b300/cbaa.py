@@ -111,6 +111,7 @@ def _signatures():
                                          ctypes.c_float, ctypes.c_uint32, vp]),
         "cbaa_mlp_to_bf16": (ctypes.c_int, [vp, vp, vp]),
         "cbaa_learned_decide": (ctypes.c_int, [vp, vp, sz, ctypes.c_uint32, ctypes.c_float, vp, vp, vp]),
+        "cbaa_learned_target": (ctypes.c_int, [vp, vp, sz, vp, vp]),
         "cbaa_get_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
     }
 

@@ -444,6 +444,11 @@ int cbaa_mlp_to_bf16(const float *dev_master, uint16_t *dev_w_bf16, void *stream
     return cuda_status(cbaa::launch_to_bf16(dev_master, dev_w_bf16, as_stream(stream)));
 }
 
+int cbaa_learned_target(const float *dev_feats, const float *dev_count, size_t n, float *dev_t, void *stream) {
+    if (n && (!dev_feats || !dev_count || !dev_t)) return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_target(dev_feats, dev_count, n, dev_t, as_stream(stream)));
+}
+
 int cbaa_learned_decide(const float *dev_y, const float *dev_feats, size_t n, uint32_t log2_g, float theta,
                         float *dev_card, uint8_t *dev_decision, void *stream) {
     if ((n && (!dev_y || !dev_feats || !dev_card || !dev_decision)) || log2_g > 31) return CBAA_ERR_INVALID_ARG;

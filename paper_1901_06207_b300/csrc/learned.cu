@@ -299,7 +299,24 @@ __global__ void k_decide(const float *__restrict__ y, const float *__restrict__ 
     }
 }
 
+// Training target of one sample: ln(1 + exact cardinality) - ln(1 + Thm. 2
+// estimate), the latter as the features carry it (feature 11 = ln(1 + est)/10).
+__global__ void k_target(const float *__restrict__ feats, const float *__restrict__ count, uint64_t n,
+                         float *__restrict__ t) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += stride)
+        t[s] = log1pf(count[s]) - 10.f * feats[s * IN + 11];
+}
+
 }  // namespace
+
+cudaError_t launch_target(const float *feats, const float *count, uint64_t n, float *t, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t want = (n + 255) / 256;
+    const uint64_t cap = (uint64_t)num_sms() * 8;
+    k_target<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(feats, count, n, t);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_features(const Geo &G, const uint32_t *cube, const uint64_t *za, const double *eps,
                             const uint32_t *ips, uint64_t n, float *feats, cudaStream_t s) {

@@ -133,9 +133,66 @@ class LearnedEstimator:
 
     @staticmethod
     def target(X, counts):
-        """Training target for exact cardinalities ``counts`` (device float): ln(1 + c) - ln(1 + est)."""
+        """Training target for exact cardinalities ``counts`` (device): ln(1 + c) - ln(1 + est), computed by
+        cbaa_learned_target."""
         torch = C._torch()
-        return (torch.log1p(counts.to(torch.float32)) - 10.0 * X[:, 11]).contiguous()
+        n = int(X.shape[0])
+        c = counts.to(torch.float32).contiguous()
+        t = torch.empty(max(n, 1), dtype=torch.float32, device=X.device)
+        C._check(C.lib().cbaa_learned_target(_ptr(X), _ptr(c), n, _ptr(t), C._stream_ptr(None)), "learned_target")
+        return t[:n]
+
+    @staticmethod
+    def training_set(cand_ips, cand_counts, ips, counts, n_samples: int, seed: int = 0):
+        """Addresses (uint32) and exact cardinalities for training, n_samples of them: up to half are the
+        candidates the detector restores at its looser bound, the real hosts among them repeated to
+        weigh as much as the phantoms (which dominate the candidates of an undersized cube); the rest
+        are present sources drawn in equal numbers from each octave of cardinality -- stratified, so
+        the octaves around theta weigh as much as the crowded low ones."""
+        cand_ips = np.asarray(cand_ips, dtype=np.uint32)
+        cand_counts = np.asarray(cand_counts, dtype=np.int64)
+        ips = np.asarray(ips, dtype=np.uint32)
+        counts = np.asarray(counts, dtype=np.int64)
+        bal = LearnedEstimator.balanced_indices(cand_counts, seed)[: n_samples // 2]
+        take_ips, take_cnt = [cand_ips[bal]], [cand_counts[bal]]
+        room = n_samples - bal.size
+        keep = ~np.isin(ips, cand_ips) & (counts > 0)
+        ips, counts = ips[keep], counts[keep]
+        octave = np.floor(np.log2(np.maximum(counts, 1))).astype(np.int64)
+        groups = [np.nonzero(octave == b)[0] for b in np.unique(octave)]
+        rng = np.random.default_rng(seed)
+        groups.sort(key=len)                      # small octaves first: what they cannot fill, others get
+        for k, grp in enumerate(groups):
+            quota = room // (len(groups) - k)
+            pick = grp if grp.size <= quota else rng.choice(grp, size=quota, replace=False)
+            take_ips.append(ips[pick])
+            take_cnt.append(counts[pick])
+            room -= pick.size
+        return np.concatenate(take_ips), np.concatenate(take_cnt)
+
+    @staticmethod
+    def choose_threshold(card, counts, theta: float, max_fnr: float | None = None, factors=None) -> float:
+        """Decision threshold factor f (decide card >= f theta), a margin chosen on the training window's
+        candidates (Eq. 2, Eq. 3 over these addresses: H = cardinality >= theta): the f that minimises
+        FNR + FPR, or with max_fnr the largest f whose FNR stays within max_fnr (fewer missed super
+        hosts bought with more false positives)."""
+        card = np.asarray(card, dtype=np.float64)
+        counts = np.asarray(counts, dtype=np.float64)
+        H = counts >= theta
+        nH = max(1, int(H.sum()))
+        grid = factors if factors is not None else np.exp(np.linspace(np.log(0.1), np.log(4.0), 81))
+        best = (float("inf"), float(grid[0]))
+        for f in grid:
+            D = card >= f * theta
+            fnr = np.count_nonzero(H & ~D) / nH
+            if max_fnr is not None:
+                if fnr <= max_fnr:
+                    best = (0.0, float(f))                    # the grid ascends: keep the largest
+                continue
+            err = fnr + np.count_nonzero(D & ~H) / nH
+            if err < best[0] - 1e-12:
+                best = (err, float(f))
+        return best[1]
 
     def weights_bf16(self) -> np.ndarray:
         return self.wb.cpu().numpy().view(np.uint16).copy()

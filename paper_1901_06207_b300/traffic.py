@@ -164,6 +164,13 @@ def spec_window_64m(seed: int = 0xC0FFEE01, scale_shift: int = 0) -> TrafficSpec
                        dup_fraction=0.30, seed=seed)
 
 
+def spec_window_256m(seed: int = 0xC0FFEE40) -> TrafficSpec:
+    """The 64M window's shape at four times its size: 256M packets, a 2^24-host Zipf(1.1) pool, 2000
+    planted hosts log-uniform in [1024, 200k], 30% duplicates (the learned estimator's workload)."""
+    return TrafficSpec(n_packets=1 << 28, n_hosts=1 << 24, n_planted=2000, planted_lo=1024, planted_hi=200_000,
+                       planted_dist="loguniform", bg_mode="per_pair", zipf_a=1.1, dup_fraction=0.30, seed=seed)
+
+
 def _planted_counts(spec: TrafficSpec) -> np.ndarray:
     u = rand_unit(spec.seed, S_PLANT_N, spec.n_planted)
     if spec.planted_dist == "uniform":

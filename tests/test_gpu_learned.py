@@ -150,3 +150,53 @@ def test_training_beats_thm2_on_held_out_window(C, oracle, geo):
     assert fpr_p > 1.0                          # the regime the network is for: phantoms swamp Thm. 2
     assert fnr_l + fpr_l < 0.1 * (fnr_p + fpr_p)
     assert fnr_l < 0.1
+
+
+def test_undersized_cube_at_theta_1024(C, oracle):
+    """The learned estimator's workload at a quarter of its traffic: 64M-packet windows of the core-network
+    shape in a cube with 2^11 columns per array and 16 sketches, so each column carries about 1.4 flows per
+    row as a 4x undersized cube does at 256M packets; theta = 1024, candidates restored at 0.8 theta,
+    training on 10^6 samples of the training window (its candidates balanced, present sources stratified by
+    octave), exact cardinalities from the oracle's counter.  On the held-out window the learned decision
+    must cut FNR + FPR (Eq. 2, Eq. 3) far below Thm. 2's, and a threshold margin chosen on the training
+    window for FNR <= 2 % must hold the test FNR near that."""
+    import torch
+    from paper_1901_06207_b300 import learned as L
+    geo, theta = C.make_params(4, 3, 1, 10, [11]), 1024
+
+    def window(seed):
+        w = T.make_window(T.spec_window_64m(seed=seed))
+        cube = C.Cube(geo)
+        cube.update_binned(_dev(w.pairs.view(np.int32)), C.UpdateWorkspace(geo, w.pairs.shape[0]))
+        ips, cnt = oracle.exact_counts(w.pairs)
+        cand = cube.detect(int(0.8 * theta), ws=C.Workspace(geo, max_candidates=1 << 20), cap=1 << 20)["ip"]
+        cand = cand.astype(np.uint32)
+        pos = np.minimum(np.searchsorted(ips, cand), ips.size - 1)
+        truth = np.where(ips[pos] == cand, cnt[pos], 0)
+        return cube, cand, truth, ips, cnt
+
+    cube, cand, truth, ips, cnt = window(0xC0FFEE41)
+    sel, sel_cnt = L.LearnedEstimator.training_set(cand, truth, ips, cnt, 10 ** 6)
+    assert sel.size == 10 ** 6
+    X = L.features(cube, theta, _dev(sel.view(np.int32)))
+    t = L.LearnedEstimator.target(X, _dev(sel_cnt.astype(np.float32)))
+    net = L.LearnedEstimator(seed=7)
+    losses = net.train(X, t, epochs=30, batch=1 << 14, lr=3e-3)
+    assert losses[-1] < 0.5 * losses[0]
+    Xc = L.features(cube, theta, _dev(cand.view(np.int32)))
+    card_tr = net.decide(net.predict(Xc), Xc, geo["log2_g"], theta)[0].cpu().numpy()
+    f_min = L.LearnedEstimator.choose_threshold(card_tr, truth, theta)
+    f_cap = L.LearnedEstimator.choose_threshold(card_tr, truth, theta, max_fnr=0.02)
+    assert f_cap <= f_min
+    del cube, X, t, Xc
+    cube, cand, truth, ips, cnt = window(0xC0FFEE40)
+    Xte = L.features(cube, theta, _dev(cand.view(np.int32)))
+    card = net.decide(net.predict(Xte), Xte, geo["log2_g"], theta)[0].cpu().numpy()
+    fnr_p, fpr_p, nH = oracle.fnr_fpr(cube.detect(theta)["ip"], ips, cnt, theta)
+    fnr_m, fpr_m, _ = oracle.fnr_fpr(cand[card >= f_min * theta], ips, cnt, theta)
+    fnr_c, fpr_c, _ = oracle.fnr_fpr(cand[card >= f_cap * theta], ips, cnt, theta)
+    print(f"theta 1024, |H|={nH}: Thm. 2 FNR {fnr_p:.4f} FPR {fpr_p:.4f} | learned (f={f_min:.3f}) FNR {fnr_m:.4f} "
+          f"FPR {fpr_m:.4f} | FNR-capped (f={f_cap:.3f}) FNR {fnr_c:.4f} FPR {fpr_c:.4f}")
+    assert fpr_p > 1.0                          # phantoms swamp Thm. 2 in the undersized cube
+    assert fnr_m + fpr_m < 0.1 * (fnr_p + fpr_p)
+    assert fnr_c < 0.05 and fpr_c < 0.25 * fpr_p
