@@ -37,11 +37,15 @@ METRIC = "packets/sec (Gpps) cube update + end-of-window detect ms; fraction of 
 
 
 def update_kernels(partitioned: bool, tuning: dict, n: int) -> int:
-    """Kernels of one update call: direct 1; partitioned count, scan, scatter, apply (with sampled
-    run capacities the apply also drains the overflow list).  One pass of up to the workspace's
-    packets; tuning and n are kept for the call sites' clarity."""
-    del tuning, n
-    return 4 if partitioned else 1
+    """Kernels of one single-cube update call of n packets (one pass of up to the workspace's
+    packets): direct 1; partitioned count, scan, scatter, apply (with sampled run capacities the apply
+    also drains the overflow list), and with the heavy-source split (on by default for row tiles and
+    passes of >= 4Mi packets) sample, histogram, select, split and expand before them."""
+    if not partitioned:
+        return 1
+    heavy = tuning.get("heavy", 0)
+    split = tuning.get("tile_kind", 0) != 1 and heavy != 1 and (heavy >= 2 or n >= 4 << 20)
+    return 9 if split else 4
 
 
 def detect_kernels(geo: dict) -> int:
@@ -617,9 +621,11 @@ def run_cbaa(args):
 
 
 def run_sharded(args):
-    """Every rank is an edge router with its own 64M-packet window; per step each rank updates its
-    cube, the ranks exchange sketch slices (all-to-all), each ORs and restores the sketches it owns,
-    and the host lists are all-gathered (shard.py).  value = packets of all ranks / step time."""
+    """Every rank is an edge router with its own 64M-packet window.  Windows are double-buffered as in the
+    plain step: window k+1's reset and update (stream 1, cube k+1 mod 2) overlap window k's global-server
+    step (stream 2) -- the all-to-all of sketch slices, the OR of the owned ones, their restoration, the
+    device all-gather of every rank's host block and the merge by ip (ShardedDetector.enqueue: no host
+    wait).  Timed with CUDA events, max over ranks; value = packets of all ranks / step time."""
     import torch
     from paper_1901_06207_b300 import cbaa as C
     from paper_1901_06207_b300.shard import ShardedDetector
@@ -633,42 +639,72 @@ def run_sharded(args):
     w = T.make_window(spec)
     n = w.pairs.shape[0]
     pairs = torch.from_numpy(w.pairs.view(np.int32)).to(dev)
-    C.set_tuning(scatter_shape=6, tile_kind=2)
-    cube = C.Cube(geo, device=dev)
+    if args.tuning:
+        C.set_tuning(**json.loads(args.tuning))
+    cubes = [C.Cube(geo, device=dev) for _ in range(2)]
     uws = C.UpdateWorkspace(geo, n, device=dev)
     det = ShardedDetector(geo, theta, rank, world, device=dev)
     stream = torch.cuda.current_stream(dev)
+    s_up, s_det = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    done = [None, None]
 
-    def step():
-        cube.reset()
-        cube.update_binned(pairs, uws)
-        return det(cube)
+    def step(k):
+        b = k & 1
+        with torch.cuda.stream(s_up):
+            if done[b] is not None:
+                s_up.wait_event(done[b])          # its previous window's exchange has read the cube
+            cubes[b].reset()
+            cubes[b].update_binned(pairs, uws)
+            up = torch.cuda.Event()
+            up.record(s_up)
+        with torch.cuda.stream(s_det):
+            s_det.wait_event(up)
+            det.enqueue(cubes[b], b)
+            done[b] = torch.cuda.Event()
+            done[b].record(s_det)
 
-    for _ in range(max(args.warmup, 1)):
-        hosts, _ = step()
-    steps = max(1, min(args.steps, 50))
+    def join():
+        stream.wait_stream(s_up)
+        stream.wait_stream(s_det)
+
+    s_up.wait_stream(stream)
+    s_det.wait_stream(stream)
+    for k in range(max(args.warmup, 3)):
+        step(k)
+    join()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 200))
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            hosts, info = step()
+        t_start.record(stream)
+        s_up.wait_stream(stream)
+        s_det.wait_stream(stream)
+        for k in range(steps):
+            step(k)
+        join()
+        t_end.record(stream)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
     barrier(world)
-    el_max = reduce_over_ranks(el, world, "max", dev)
+    ms = reduce_over_ranks(t_start.elapsed_time(t_end), world, "max", dev)
+    hosts, info = det.result((steps - 1) & 1)
+    assert info["status"] == C.OK, info
     packets_all = reduce_over_ranks(float(n), world, "sum", dev)
-    value = packets_all * steps / el_max / 1e9
+    value = packets_all * steps / (ms * 1e-3) / 1e9
+    words = C.cube_bytes(geo) // 4
     line = {"metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": el_max * 1e3 / steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {**desc, "workload": "sharded_64m_per_rank",
-                       "step": "reset, update the rank's cube, all-to-all of sketch slices, OR of the owned "
-                               "sketches, restore them, all-gather of the host lists (host-synchronous, "
-                               "timed on the host clock)",
+                       "step": "double-buffered: a window's reset and update (stream 1) overlap the previous "
+                               "window's all-to-all of sketch slices, OR of the owned ones, restoration, "
+                               "device all-gather of the host blocks and merge by ip (stream 2); no host wait",
                        "parallelism": f"{world} ranks, sketches split {1 << geo['r']} / {world}"},
+            "all_to_all_bytes_per_rank": {"sent": 4 * words * (world - 1) // world,
+                                          "received": 4 * words * (world - 1) // world},
             "hosts_detected": int(hosts.size),
-            "gpu_launches": steps * (update_kernels(True, C.get_tuning(), n) + detect_kernels(geo) +
+            "gpu_launches": steps * (update_kernels(True, C.get_tuning(), n) + detect_kernels(geo) + 2 +
                                      (1 if world > 1 else 0)),
             "clocks": clocks.summary()}
     if rank == 0:
@@ -956,7 +992,8 @@ def run_batched(args):
                       "or_into": {"call": "cbaa_cube_merge", "ms": merge_or_ms, "bytes": merge_or_bytes,
                                   "frac": merge_or_bytes / (merge_or_ms * 1e-3) / 1e9 / hbm_peak}},
             "hosts_per_window": [int(i["n_hosts"]) for _, i in res],
-            "gpu_launches": steps * len(wins) * (update_kernels(True, C.get_tuning(), sum(n_per) // len(wins)) + 1 +
+            # a pass over several router cubes takes no heavy split; the merge is inside it
+            "gpu_launches": steps * len(wins) * (update_kernels(True, {**C.get_tuning(), "heavy": 1}, 0) +
                                                  detect_kernels(geo)),
             "clocks": clocks.summary()}
     if rank == 0:

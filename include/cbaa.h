@@ -291,6 +291,18 @@ int cbaa_detect_range_async(const cbaa_cube *cube, uint32_t cs_lo, uint32_t cs_h
  * not among srcs; k = 0 or words = 0 is a no-op. */
 int cbaa_or_words(uint32_t *dst, const uint32_t *const *srcs, int k, size_t words, void *stream);
 
+/* The global server's host list from its owners' (Section III.C split by
+ * sketch), async: k host lists, each sorted by ip, in dev_blocks (block j =
+ * dev_blocks[j * block_cap ...], its count in dev_infos[j].n_hosts, at most
+ * block_cap used), merged into dev_out sorted by ip (the first out_cap
+ * records).  The lists must hold disjoint addresses, as the owners of
+ * disjoint sketch ranges do.  dev_info_out: the first status that is not
+ * CBAA_OK (CBAA_ERR_CAPACITY also when the merged list exceeds out_cap), and
+ * the sums of n_hosts, n_hot and n_tuples.  For all-gathered
+ * cbaa_detect_range_async results, so that no host round trip is needed. */
+int cbaa_merge_hosts(const cbaa_host *dev_blocks, size_t block_cap, int k, const cbaa_detect_info *dev_infos,
+                     cbaa_host *dev_out, size_t out_cap, cbaa_detect_info *dev_info_out, void *stream);
+
 /* Same as cbaa_detect_async followed by the copy of the records to host_out
  * (room for cap) and *n_out = number of hosts found; sync.  Returns
  * CBAA_ERR_CAPACITY when n_hosts > cap (the first cap records are valid) and

@@ -112,6 +112,7 @@ def _signatures():
         "cbaa_mlp_to_bf16": (ctypes.c_int, [vp, vp, vp]),
         "cbaa_learned_decide": (ctypes.c_int, [vp, vp, sz, ctypes.c_uint32, ctypes.c_float, vp, vp, vp]),
         "cbaa_learned_target": (ctypes.c_int, [vp, vp, sz, vp, vp]),
+        "cbaa_merge_hosts": (ctypes.c_int, [vp, sz, ctypes.c_int, vp, vp, sz, vp, vp]),
         "cbaa_get_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
     }
 
@@ -406,6 +407,16 @@ def or_words(dst, srcs, stream=None):
             raise ValueError("or_words: every source must have dst's length")
     arr = (ctypes.c_void_p * max(1, len(srcs)))(*[t.data_ptr() for t in srcs])
     _check(lib().cbaa_or_words(dst.data_ptr(), arr, len(srcs), words, _stream_ptr(stream)), "or_words")
+
+
+def merge_hosts(blocks, infos, out, info_out, stream=None):
+    """Merge k owners' sorted host lists: ``blocks`` int32 [k, 4 * cap] (cbaa_host records), ``infos``
+    int32 [k, 8] (cbaa_detect_info), into ``out`` int32 [4 * out_cap] and ``info_out`` int32 [8]."""
+    k = int(blocks.shape[0])
+    cap = blocks.shape[1] * blocks.element_size() // 16
+    out_cap = out.numel() * out.element_size() // 16
+    _check(lib().cbaa_merge_hosts(blocks.data_ptr(), cap, k, infos.data_ptr(), out.data_ptr(), out_cap,
+                                  info_out.data_ptr(), _stream_ptr(stream)), "merge_hosts")
 
 
 def hosts_from_device(out, info) -> tuple[np.ndarray, dict]:

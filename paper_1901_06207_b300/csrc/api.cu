@@ -368,6 +368,15 @@ int cbaa_detect_range_async(const cbaa_cube *cube, uint32_t cs_lo, uint32_t cs_h
                                 cbaa::num_sms(), as_stream(stream), cs_lo, cs_hi);
 }
 
+int cbaa_merge_hosts(const cbaa_host *dev_blocks, size_t block_cap, int k, const cbaa_detect_info *dev_infos,
+                     cbaa_host *dev_out, size_t out_cap, cbaa_detect_info *dev_info_out, void *stream) {
+    if (k < 1 || block_cap > 0xFFFFFFFFull || !dev_infos || !dev_info_out || (block_cap && !dev_blocks) ||
+        (out_cap && !dev_out))
+        return CBAA_ERR_INVALID_ARG;
+    return cuda_status(cbaa::launch_merge_hosts(dev_blocks, (uint32_t)block_cap, (uint32_t)k, dev_infos, dev_out,
+                                                out_cap, dev_info_out, as_stream(stream)));
+}
+
 int cbaa_or_words(uint32_t *dst, const uint32_t *const *srcs, int k, size_t words, void *stream) {
     if (k < 0 || (k > 0 && words > 0 && (!dst || !srcs))) return CBAA_ERR_INVALID_ARG;
     if (k == 0 || words == 0) return CBAA_OK;

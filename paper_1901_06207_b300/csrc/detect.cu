@@ -430,4 +430,68 @@ int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws,
     return CBAA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Host lists of several owners (ranks that restored disjoint sketch ranges,
+// Section III.C's global server split by sketch), each sorted by ip in its
+// own block of `cap` records with its count in infos[j].n_hosts, merged into
+// one list sorted by ip.  The owners' addresses are disjoint, so a record's
+// place is its index in its list plus, for every other list, the number of
+// records with a smaller ip (a binary search each).  One thread per record.
+__global__ void k_merge_hosts(const cbaa_host *__restrict__ blocks, uint32_t cap, uint32_t k,
+                              const cbaa_detect_info *__restrict__ infos, cbaa_host *__restrict__ out,
+                              uint64_t out_cap) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (uint64_t)k * cap; t += stride) {
+        const uint32_t j = (uint32_t)(t / cap), i = (uint32_t)(t - (uint64_t)j * cap);
+        const uint32_t nj = infos[j].n_hosts < cap ? infos[j].n_hosts : cap;
+        if (i >= nj) continue;
+        const cbaa_host h = blocks[t];
+        uint64_t place = i;
+        for (uint32_t o = 0; o < k; ++o) {
+            if (o == j) continue;
+            const cbaa_host *b = blocks + (uint64_t)o * cap;
+            uint32_t lo = 0, hi = infos[o].n_hosts < cap ? infos[o].n_hosts : cap;
+            while (lo < hi) {                              // first record of list o with ip >= h.ip
+                const uint32_t mid = (lo + hi) >> 1;
+                if (b[mid].ip < h.ip) lo = mid + 1; else hi = mid;
+            }
+            place += lo;
+        }
+        if (place < out_cap) out[place] = h;
+    }
+}
+
+// The merged list's info: the first status that is not OK (CAPACITY when
+// the merged list exceeds out_cap), and the sums of the counts (n_hosts
+// counts every host, also past any capacity).
+__global__ void k_merge_infos(const cbaa_detect_info *__restrict__ infos, uint32_t k, uint64_t out_cap,
+                              cbaa_detect_info *__restrict__ out) {
+    if (threadIdx.x != 0) return;
+    cbaa_detect_info r = {};
+    r.status = CBAA_OK;
+    for (uint32_t j = 0; j < k; ++j) {
+        const cbaa_detect_info x = infos[j];
+        if (r.status == CBAA_OK && x.status != CBAA_OK) r.status = x.status;
+        r.n_hosts += x.n_hosts;
+        r.n_hot += x.n_hot;
+        r.n_tuples += x.n_tuples;
+        r.need_tuples = r.need_tuples > x.need_tuples ? r.need_tuples : x.need_tuples;
+    }
+    if (r.status == CBAA_OK && r.n_hosts > out_cap) r.status = CBAA_ERR_CAPACITY;
+    *out = r;
+}
+
+cudaError_t launch_merge_hosts(const cbaa_host *blocks, uint32_t cap, uint32_t k, const cbaa_detect_info *infos,
+                               cbaa_host *out, uint64_t out_cap, cbaa_detect_info *info_out, cudaStream_t s) {
+    const uint64_t total = (uint64_t)k * cap;
+    if (total) {
+        const uint64_t want = (total + 255) / 256, lim = (uint64_t)num_sms() * 8;
+        k_merge_hosts<<<(unsigned)(want < lim ? want : lim), 256, 0, s>>>(blocks, cap, k, infos, out, out_cap);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_merge_infos<<<1, 32, 0, s>>>(infos, k, out_cap, info_out);
+    return cudaGetLastError();
+}
+
 }  // namespace cbaa

@@ -118,6 +118,10 @@ inline WsPtrs ws_pointers(const Geo &G, const WsLayout &L, void *base) {
 }
 
 // Restoration of the sketches [cs_lo, cs_hi) (cs_hi = 0: all of them).
+// Merge k owners' sorted host lists (blocks of cap records, counts in infos)
+// into out (room for out_cap) sorted by ip, and their infos into info_out.
+cudaError_t launch_merge_hosts(const cbaa_host *blocks, uint32_t cap, uint32_t k, const cbaa_detect_info *infos,
+                               cbaa_host *out, uint64_t out_cap, cbaa_detect_info *info_out, cudaStream_t s);
 int detect_enqueue(const Geo &G, const uint32_t *cube, uint32_t theta, void *ws, size_t ws_bytes,
                    cbaa_host *out, uint64_t cap, cbaa_detect_info *info_copy, int num_sms, cudaStream_t s,
                    uint32_t cs_lo = 0, uint32_t cs_hi = 0);

@@ -9,7 +9,9 @@ rank the N copies of its own sketches; it ORs them (cbaa_or_words -- NCCL
 has no bitwise-OR reduction) and restores its sketches alone
 (cbaa_detect_range_async).  Detection is independent per sketch (each has
 its own eps and Zmax), so the owners' host lists together are the global
-list; they are all-gathered and merged by ip.
+list; they are all-gathered and merged by ip -- on the host (restore), or
+device to device and merged by a kernel with no host wait (enqueue), so a
+window's exchange and restoration overlap the next window's update.
 
 Orchestration only: the OR and the restoration run in libcbaa's kernels, the
 exchange and the gathers are torch.distributed collectives.  The two
@@ -69,6 +71,19 @@ def gather_hosts(hosts: np.ndarray, rank: int, world: int, device, group=None) -
     return np.sort(out, order="ip")
 
 
+def gather_blocks(block, info, out_blocks, out_infos, world: int, group=None):
+    """All-gather, device to device, every rank's fixed-capacity block of host records and its info
+    words: rank j's land in out_blocks[j] and out_infos[j] (shapes [world, ...]).  No host round trip:
+    the counts travel inside the info words and are read by the merge kernel."""
+    import torch.distributed as dist
+    if world == 1:
+        out_blocks[0].copy_(block)
+        out_infos[0].copy_(info)
+        return
+    dist.all_gather(list(out_blocks.unbind(0)), block, group=group)
+    dist.all_gather(list(out_infos.unbind(0)), info, group=group)
+
+
 class ShardedDetector:
     """The global server's restoration split over the ranks of a process group."""
 
@@ -82,6 +97,12 @@ class ShardedDetector:
         self.ws = C.Workspace(geo, max_candidates=max_candidates, device=device)
         self.out = torch.zeros(4 * cap, dtype=torch.int32, device=device)
         self.info = torch.zeros(8, dtype=torch.int32, device=device)
+        # the asynchronous path: gathered blocks, and two result slots (one window restored while the
+        # previous one's list is read)
+        self.gath = torch.zeros((world, 4 * cap), dtype=torch.int32, device=device)
+        self.ginfo = torch.zeros((world, 8), dtype=torch.int32, device=device)
+        self.res = [torch.zeros(4 * cap * world, dtype=torch.int32, device=device) for _ in range(2)]
+        self.res_info = [torch.zeros(8, dtype=torch.int32, device=device) for _ in range(2)]
 
     def merge(self, cube: "C.Cube"):
         """After this, ``cube`` holds, in this rank's sketches, the OR of every rank's cube."""
@@ -98,3 +119,16 @@ class ShardedDetector:
     def __call__(self, cube: "C.Cube") -> tuple[np.ndarray, dict]:
         self.merge(cube)
         return self.restore(cube)
+
+    def enqueue(self, cube: "C.Cube", slot: int):
+        """The whole global-server step on the current stream, with no host wait: the sketch exchange
+        and OR, the restoration of this rank's sketches, the device all-gather of every rank's hosts
+        and info, and their merge by ip (cbaa_merge_hosts) into result slot ``slot`` (0 or 1)."""
+        self.merge(cube)
+        cube.detect_range_async(self.lo, self.hi, self.theta, self.ws, self.out, self.info)
+        gather_blocks(self.out, self.info, self.gath, self.ginfo, self.world, self.group)
+        C.merge_hosts(self.gath, self.ginfo, self.res[slot], self.res_info[slot])
+
+    def result(self, slot: int) -> tuple[np.ndarray, dict]:
+        """The global host list of the window last enqueued into ``slot`` (synchronises)."""
+        return C.hosts_from_device(self.res[slot], self.res_info[slot])

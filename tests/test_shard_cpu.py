@@ -52,7 +52,16 @@ def _rank_main(rank, world, port, words, out):
 
     own = shard.exchange_slices(mem, rank, world, recv, or_fn)
     got = shard.gather_hosts(_hosts(rank, 3 + 5 * rank), rank, world, "cpu")
-    out[rank] = (own.numpy().view(np.uint32).copy(), got)
+    # the asynchronous path's gather: fixed-capacity blocks and info words, tensor to tensor
+    cap = 16
+    block = torch.zeros(4 * cap, dtype=torch.int32)
+    h = _hosts(rank, 3 + 5 * rank)[:cap]
+    block[:4 * h.size] = torch.from_numpy(h.view(np.int32).copy())
+    info = torch.tensor([0, h.size, rank, 0, 0, 0, 0, 0], dtype=torch.int32)
+    blocks = torch.zeros((world, 4 * cap), dtype=torch.int32)
+    infos = torch.zeros((world, 8), dtype=torch.int32)
+    shard.gather_blocks(block, info, blocks, infos, world)
+    out[rank] = (own.numpy().view(np.uint32).copy(), got, blocks.numpy().copy(), infos.numpy().copy())
     dist.destroy_process_group()
 
 
@@ -69,9 +78,13 @@ def test_exchange_and_gather(world):
         full |= _words(r, words)
     want_hosts = np.sort(np.concatenate([_hosts(r, 3 + 5 * r) for r in range(world)]), order="ip")
     for r in range(world):
-        own, got = out[r]
+        own, got, blocks, infos = out[r]
         assert np.array_equal(own, full[r * per:(r + 1) * per]), r
         assert np.array_equal(got, want_hosts), r
+        for j in range(world):                    # every rank holds every rank's block and count
+            hj = _hosts(j, 3 + 5 * j)[:16]
+            assert infos[j, 1] == hj.size and infos[j, 2] == j
+            assert np.array_equal(blocks[j].view(np.uint8).view(want_hosts.dtype)[:hj.size], hj)
 
 
 def test_owned_ranges_partition_the_sketches():
