@@ -226,97 +226,67 @@ __device__ __forceinline__ uint32_t split_load(const uint32_t *pairs, uint64_t n
     return ok;
 }
 
-// Every warp walks its own chunks of 256 packets (chunk c for c = global
-// warp, + all warps, ...), the next chunk's loads in flight while it works
-// on the current one.  Shared memory: the lookup table, then K row bitmaps
-// of W words (kwords words).  Residual entries go to this block's region
-// (rcap entries from blockIdx.x * rcap), one shared-memory reservation per
-// warp and chunk; the region's count is written at the end.
-template <uint32_t THREADS, uint32_t MINB, bool ORIENT>
-__global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, const uint32_t *__restrict__ pairs,
-                                                               uint64_t n, const uint32_t *__restrict__ tab_g,
-                                                               uint32_t kwords, uint32_t *__restrict__ bits_g,
-                                                               uint2 *__restrict__ resid, uint64_t rcap,
-                                                               uint32_t *__restrict__ rcount) {
-    extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t *tab = sm;
-    uint32_t *bm = sm + kTabWords;
-    __shared__ uint32_t s_cnt;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u;
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(tab_g);
-        uint4 *dst = reinterpret_cast<uint4 *>(tab);
-        for (uint32_t i = tid; i < kTabWords / 4; i += THREADS) dst[i] = __ldg(src + i);
-        uint4 *b4 = reinterpret_cast<uint4 *>(bm);
-        for (uint32_t i = tid; i < kwords / 4; i += THREADS) b4[i] = make_uint4(0u, 0u, 0u, 0u);
-        if (tid == 0) s_cnt = 0;
+// The split of NP packets per lane of a warp (slot k of lane `lane`: a[k],
+// b[k], present when bit k of ok is set): hashes; lookups; bitmap words of
+// the heavy ones, read together; sets of the bits still clear; the others'
+// entries {mangled ip, row} written to `region` at places reserved with one
+// shared-memory atomic per warp.  In phases, so that the lanes' shared-memory
+// reads are in flight together.
+template <uint32_t NP, bool ORIENT>
+__device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab, uint32_t *bm, uint32_t (&a)[NP],
+                                              uint32_t (&b)[NP], uint32_t ok, uint2 *region, uint32_t *s_cnt,
+                                              uint32_t lane) {
+    uint32_t m[NP], row[NP], h[NP];
+#pragma unroll
+    for (uint32_t k = 0; k < NP; ++k) {
+        if (ORIENT && ((ok >> k) & 1u) && !orient(G, a[k], b[k])) ok &= ~(1u << k);   // raw {src, dst} vs NI
+        m[k] = mangle(G, a[k]);
+        row[k] = row_of(G, b[k]);
     }
-    __syncthreads();
-    uint2 *region = resid + (uint64_t)blockIdx.x * rcap;
-    const bool al = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
-    const uint64_t chunks = (n + 255) / 256;
-    const uint64_t nw = (uint64_t)gridDim.x * (THREADS / 32);
-    uint64_t c = (uint64_t)blockIdx.x * (THREADS / 32) + (tid >> 5);
-    uint4 q[4], qn[4];
-    uint32_t ok = c < chunks ? split_load(pairs, n, c, lane, al, q) : 0u;
-    for (; c < chunks; c += nw) {
-        const uint32_t okn = c + nw < chunks ? split_load(pairs, n, c + nw, lane, al, qn) : 0u;
-        // in phases, so that the eight packets' shared-memory reads are in flight together:
-        // hashes; lookups; bitmap words of the heavy ones; sets of the bits still clear
-        uint32_t m[8], row[8], h[8];
 #pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) {
-            uint32_t a = (k & 1u) ? q[k / 2].z : q[k / 2].x;
-            uint32_t b = (k & 1u) ? q[k / 2].w : q[k / 2].y;
-            if (ORIENT && ((ok >> k) & 1u) && !orient(G, a, b)) ok &= ~(1u << k);   // raw {src, dst} against NI
-            m[k] = mangle(G, a);
-            row[k] = row_of(G, b);
+    for (uint32_t k = 0; k < NP; ++k) h[k] = heavy_index(tab, m[k]);
+    uint32_t heavy = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < NP; ++k) {
+        if (((ok >> k) & 1u) && h[k] < kHeavyIdxMask) {
+            heavy |= 1u << k;
+            h[k] = h[k] * G.W + (row[k] >> 5);                // the bitmap word
         }
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) h[k] = heavy_index(tab, m[k]);
-        uint32_t heavy = 0;
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) {
-            if (((ok >> k) & 1u) && h[k] < kHeavyIdxMask) {
-                heavy |= 1u << k;
-                h[k] = h[k] * G.W + (row[k] >> 5);            // the bitmap word
-            }
-        }
-        uint32_t wv[8];
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) wv[k] = ((heavy >> k) & 1u) ? bm[h[k]] : 0xFFFFFFFFu;
-        // a stale read only costs an atomic that changes nothing: every set is an OR
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) {
-            const uint32_t bit = 1u << (row[k] & 31u);
-            if (!(wv[k] & bit)) atomicOr(&bm[h[k]], bit);
-        }
-        const uint32_t keep = ok & ~heavy;
-        const uint32_t cnt = __popc(keep);
-        // this warp's entries: lane prefix, one reservation in the block's region
-        uint32_t x = cnt;
-#pragma unroll
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        uint32_t base = 0;
-        if (lane == 31 && x) base = atomicAdd(&s_cnt, x);
-        base = __shfl_sync(0xffffffffu, base, 31) + x - cnt;
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k)
-            if ((keep >> k) & 1u) region[base + __popc(keep & ((1u << k) - 1u))] = make_uint2(m[k], row[k]);
-#pragma unroll
-        for (uint32_t j = 0; j < 4; ++j) q[j] = qn[j];
-        ok = okn;
     }
-    // the region's count, then the block's bitmaps into the global ones: one
-    // bulk OR reduction (async proxy), after the shared-memory writes are
-    // made visible to it
+    uint32_t wv[NP];
+#pragma unroll
+    for (uint32_t k = 0; k < NP; ++k) wv[k] = ((heavy >> k) & 1u) ? bm[h[k]] : 0xFFFFFFFFu;
+    // a stale read only costs an atomic that changes nothing: every set is an OR
+#pragma unroll
+    for (uint32_t k = 0; k < NP; ++k) {
+        const uint32_t bit = 1u << (row[k] & 31u);
+        if (!(wv[k] & bit)) atomicOr(&bm[h[k]], bit);
+    }
+    const uint32_t keep = ok & ~heavy;
+    const uint32_t cnt = __popc(keep);
+    uint32_t x = cnt;                                          // lane prefix, one reservation per warp
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t base = 0;
+    if (lane == 31 && x) base = atomicAdd(s_cnt, x);
+    base = __shfl_sync(0xffffffffu, base, 31) + x - cnt;
+#pragma unroll
+    for (uint32_t k = 0; k < NP; ++k)
+        if ((keep >> k) & 1u) region[base + __popc(keep & ((1u << k) - 1u))] = make_uint2(m[k], row[k]);
+}
+
+// End of a split block: the region's count, then the block's bitmaps into the
+// global ones, one bulk OR reduction (async proxy) after the shared-memory
+// writes are made visible to it.
+__device__ __forceinline__ void split_flush(const uint32_t *bm, uint32_t kwords, uint32_t *bits_g,
+                                            const uint32_t *s_cnt, uint32_t *rcount) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-        rcount[blockIdx.x] = s_cnt;
+    __syncthreads();                                  // every warp's reservations and bit sets are done
+    if (threadIdx.x == 0) {
+        rcount[blockIdx.x] = *s_cnt;
         constexpr uint32_t kChunk = 32u << 10;
         const uint32_t bytes = kwords * 4u;
         const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(bm));
@@ -328,6 +298,60 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
+}
+
+// Loads the lookup table and clears the bitmaps in shared memory.
+template <uint32_t THREADS>
+__device__ __forceinline__ void split_prologue(const uint32_t *tab_g, uint32_t *tab, uint32_t *bm, uint32_t kwords) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(tab_g);
+    uint4 *dst = reinterpret_cast<uint4 *>(tab);
+    for (uint32_t i = threadIdx.x; i < kTabWords / 4; i += THREADS) dst[i] = __ldg(src + i);
+    uint4 *b4 = reinterpret_cast<uint4 *>(bm);
+    for (uint32_t i = threadIdx.x; i < kwords / 4; i += THREADS) b4[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Every warp walks its own chunks of 256 packets (chunk c for c = global
+// warp, + all warps, ...), the next chunk's 16-byte loads in flight in
+// registers while it works on the current one.  Shared memory: the lookup
+// table, then K row bitmaps of W words (kwords words).  Residual entries go
+// to this block's region (rcap entries from blockIdx.x * rcap), one
+// shared-memory reservation per warp and chunk; the region's count is
+// written at the end.
+template <uint32_t THREADS, uint32_t MINB, bool ORIENT>
+__global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, const uint32_t *__restrict__ pairs,
+                                                               uint64_t n, const uint32_t *__restrict__ tab_g,
+                                                               uint32_t kwords, uint32_t *__restrict__ bits_g,
+                                                               uint2 *__restrict__ resid, uint64_t rcap,
+                                                               uint32_t *__restrict__ rcount) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *tab = sm;
+    uint32_t *bm = sm + kTabWords;
+    __shared__ uint32_t s_cnt;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    split_prologue<THREADS>(tab_g, tab, bm, kwords);
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    uint2 *region = resid + (uint64_t)blockIdx.x * rcap;
+    const bool al = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
+    const uint64_t chunks = (n + 255) / 256;
+    const uint64_t nw = (uint64_t)gridDim.x * (THREADS / 32);
+    uint64_t c = (uint64_t)blockIdx.x * (THREADS / 32) + (tid >> 5);
+    uint4 q[4], qn[4];
+    uint32_t ok = c < chunks ? split_load(pairs, n, c, lane, al, q) : 0u;
+    for (; c < chunks; c += nw) {
+        const uint32_t okn = c + nw < chunks ? split_load(pairs, n, c + nw, lane, al, qn) : 0u;
+        uint32_t a[8], b[8];
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) {
+            a[k] = (k & 1u) ? q[k / 2].z : q[k / 2].x;
+            b[k] = (k & 1u) ? q[k / 2].w : q[k / 2].y;
+        }
+        split_packets<8, ORIENT>(G, tab, bm, a, b, ok, region, &s_cnt, lane);
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) q[j] = qn[j];
+        ok = okn;
+    }
+    split_flush(bm, kwords, bits_g, &s_cnt, rcount);
 }
 
 // One warp per (heavy source, array): the source's row bitmap ORed into its
