@@ -53,12 +53,13 @@ def detect_kernels(geo: dict) -> int:
     return 3 + (geo["n_ra"] - 1)
 
 
-def workload(name: str):
+def workload(name: str, scale_shift: int = 0):
     from paper_1901_06207_b300.cbaa import make_params
     if name == "window64m":
         geo = make_params(5, 3, 1, 10, [12])
-        spec = T.spec_window_64m()
-        desc = dict(workload="window_64m_l2_cube", packets_per_window=spec.n_packets, source_pool=spec.n_hosts,
+        spec = T.spec_window_64m(scale_shift=scale_shift)
+        desc = dict(workload="window_64m_l2_cube" if scale_shift == 0 else f"window_64m_l2_cube/2^{scale_shift}",
+                    packets_per_window=spec.n_packets, source_pool=spec.n_hosts,
                     planted_super_hosts=spec.n_planted, planted_peers="log-uniform [1024, 200000]",
                     background="Zipf(1.1) sources over the pool, uniform 2^32 peers", duplicate_fraction=0.3,
                     theta=1024, geometry="r=5, |RA|=3, |VA|=1, g=2^10, c=2^12 (64 MiB cube)")
@@ -251,7 +252,7 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    geo, spec, theta, desc = workload(args.workload)
+    geo, spec, theta, desc = workload(args.workload, args.scale_shift)
     w = T.make_window(spec)
     n_sample = min(spec.n_packets, args.reference_sample)
     for _ in range(args.warmup):
@@ -307,7 +308,7 @@ def run_cbaa(args):
     torch.cuda.set_device(local)
     dist_init(world, "nccl")
     dev = torch.device("cuda", local)
-    geo, spec0, theta, desc = workload(args.workload)
+    geo, spec0, theta, desc = workload(args.workload, args.scale_shift)
     spec = spec0 if rank == 0 else T.TrafficSpec(**{**spec0.__dict__, "seed": spec0.seed + 0x100 * rank})
     w = T.make_window(spec)
     n = w.pairs.shape[0]
@@ -325,7 +326,7 @@ def run_cbaa(args):
         tuned, path = None, args.update            # library default shapes, or --tuning
         if args.tuning:
             C.set_tuning(**json.loads(args.tuning))
-    uws = C.UpdateWorkspace(geo, n, device=dev) if path == "binned" else None
+    uws = C.UpdateWorkspace(geo, args.workspace_packets or n, device=dev) if path == "binned" else None
     cap = 1 << 16
     out = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
     info = torch.zeros(8, dtype=torch.int32, device=dev)
@@ -548,7 +549,8 @@ def run_cbaa(args):
 
     hbm_peak, hbm_src = measured_peaks()
     upd_s = statistics.mean(upd_ms) * 1e-3
-    traffic = load_traffic(args.workload, path)
+    # the committed counters describe one pass over a whole default window
+    traffic = None if (args.workspace_packets or args.scale_shift) else load_traffic(args.workload, path)
     line = {
         "metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -557,7 +559,8 @@ def run_cbaa(args):
                                  "the 64 MiB cubes are L2-resident by design and re-zeroed every step",
                    "pipelining": "double-buffered windows: a window's update (stream 1, cube k mod 2) overlaps "
                                  "the previous window's detect and the reset that follows it (stream 2)",
-                   "parallelism": "one window per rank" if world > 1 else "single GPU"},
+                   "parallelism": "one window per rank" if world > 1 else "single GPU",
+                   **({"update_workspace_packets": args.workspace_packets} if args.workspace_packets else {})},
         "serial": {"ms_per_window": serial_ms, "value": n / (serial_ms * 1e-3) / 1e9, "unit": "Gpps",
                    "steps": n_serial, "note": "one window at a time on one stream (reset, update, detect)"},
         "update_ms": statistics.mean(upd_ms), "update_gpps": n / upd_s / 1e9,
@@ -1131,6 +1134,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="packets of the window the cpu_baseline oracle run takes (0: the whole window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workspace-packets", type=int, default=0,
+                    help="window workloads: size the update workspace for this many packets (0: the window); "
+                         "fewer than a window makes the update run in several passes")
+    ap.add_argument("--scale-shift", type=int, default=0,
+                    help="window64m: the same window shape at 2^-k the packets and pool (small profiling cases)")
     ap.add_argument("--learned-size", default="full", choices=["full", "scaled"],
                     help="learned workload: 256M-packet windows (full) or 64M with the same column load")
     args = ap.parse_args()
