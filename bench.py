@@ -332,7 +332,9 @@ def run_cbaa(args):
     info = torch.zeros(8, dtype=torch.int32, device=dev)
     # update (direct: 1 kernel; binned: count, scan, scatter, apply) | detect: zero counts, eps/zmax,
     # hot lists, |RA|-1 joins, rank sort, sort/status
-    kernels_per_step = update_kernels(uws is not None, C.get_tuning(), n) + detect_kernels(geo)
+    pass_n = min(n, args.workspace_packets or n) if uws is not None else n
+    kernels_per_step = -(-n // pass_n) * update_kernels(uws is not None, C.get_tuning(), pass_n) + \
+        detect_kernels(geo)
 
     def do_update(c=None, src=None):
         c = cube if c is None else c
@@ -582,7 +584,9 @@ def run_cbaa(args):
             "worst_ms": tuned["worst_ms"], "candidates": tuned["candidates"]},
         "tuning": C.get_tuning(),
         "roofline": {"bound": "hbm", "kernel": f"update ({path}: " +
-                     ("count+scan+scatter+apply" if uws is not None else "k_update") + ")",
+                     ({9: "heavy sample+hist+select+split+expand, residual count+scan+scatter+apply",
+                       4: "count+scan+scatter+apply", 1: "k_update"}[
+                         update_kernels(uws is not None, C.get_tuning(), pass_n)]) + ")",
                      "achieved": 8 * n / upd_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": 8 * n / upd_s / 1e9 / hbm_peak,
                      "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})",
