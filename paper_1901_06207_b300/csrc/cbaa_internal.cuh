@@ -49,6 +49,18 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     return x;
 }
 
+// mix32 without its last step, for callers that keep only bits 16..31 of the
+// result: the last step XORs x >> 16 into bits 0..15 and leaves bits 16..31
+// as they are, so mix32(x) >> s == mix32_top(x) >> s for every s >= 16.  The
+// row hash keeps the top log2 g <= 15 bits and the VA hash the top cbn <= 16.
+__host__ __device__ __forceinline__ uint32_t mix32_top(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    return x;
+}
+
 // Inverse multipliers modulo 2^32 (a * a^-1 == 1), fixed at compile time by
 // Newton's iteration on the host compiler.
 constexpr uint32_t inv_odd(uint32_t a) {
@@ -75,12 +87,12 @@ __host__ __device__ __forceinline__ uint32_t unmangle(const Geo &G, uint32_t m) 
 
 // bvIdx = H_bv(oip): top log2_g bits of the finaliser.
 __host__ __device__ __forceinline__ uint32_t row_of(const Geo &G, uint32_t oip) {
-    return mix32(oip ^ G.seed_bv) >> (32u - G.log2_g);
+    return mix32_top(oip ^ G.seed_bv) >> (32u - G.log2_g);     // shift >= 17
 }
 
 // CL(j) = H_j(LP) for validating array j (array index n_ra + j).
 __host__ __device__ __forceinline__ uint32_t va_col(const Geo &G, uint32_t j, uint32_t lp) {
-    return mix32(lp ^ G.seed_va[j]) >> (32u - G.cbn[G.n_ra + j]);
+    return mix32_top(lp ^ G.seed_va[j]) >> (32u - G.cbn[G.n_ra + j]);   // shift >= 16
 }
 
 // CL(i) for restoring array i: cbn(i) bits of the L-bit ring LP starting at

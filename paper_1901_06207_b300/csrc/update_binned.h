@@ -39,10 +39,11 @@ inline size_t bin_align(size_t x) { return (x + 255) / 256 * 256; }
 // law); all |RA|+|VA| columns of a source receive the same row bits (Alg. 1),
 // so a heavy source's packets are gathered in one row bitmap of W words in
 // shared memory and ORed into its columns once.  Tables:
-//   a sample table of 2^15 slots (count, last key) indexed by the top 15 bits of
-//   the mangled address, a lookup image of 2^14 entries (top 14 bits of the
-//   mangled address -> its low 18 bits << 14 | heavy index), the heavy
-//   sources' mangled addresses, their row bitmaps, and counters.
+//   a sample table of 2^15 slots (count, a key) indexed by the top 15 bits of
+//   the source key (a multiplicative bijection of the inner address), a
+//   lookup image of 2^14 entries (top 14 bits of the key -> its low 18 bits
+//   << 14 | heavy index), the heavy sources' keys, their row bitmaps, and
+//   counters.
 constexpr uint32_t kHeavyCountBits = 15;
 constexpr uint32_t kHeavyTabBits = 14;
 constexpr uint32_t kHeavyTagBits = 32 - kHeavyTabBits;            // 18
@@ -64,7 +65,7 @@ constexpr uint32_t kHeavyRegionAlign = 16384;                      // region cap
 struct HeavyWs {
     uint32_t *count, *key;        // sample table [2^kHeavyCountBits]
     uint32_t *tab;                // lookup image [2^kHeavyTabBits]
-    uint32_t *list;               // mangled address of heavy source h [kHeavyMax]
+    uint32_t *list;               // key of heavy source h [kHeavyMax]
     uint32_t *bits;               // row bitmaps [kHeavyMax][W]
     uint32_t *ctr;                // counters [kHeavyCtrWords]
     uint32_t *rcount() const { return ctr + kHeavyCtrRegions; }
@@ -109,7 +110,7 @@ inline uint32_t bin_ws_tables(const Geo &G, uint32_t n_cubes) {
 }
 
 // Words of the code buffer per packet a workspace is sized for: A codes
-// (column tiles), or a residual entry {mangled ip, row} of the heavy split
+// (column tiles), or a residual entry {iip, row} of the heavy split
 // (2 words) plus a record and an overflow entry of the row-tile pass.
 inline size_t bin_ws_words_per_pair(const Geo &G) { return (size_t)G.A + 2; }
 
@@ -171,8 +172,8 @@ struct Residual {
 // at most), with run capacities from a sample when `sampled`; W.codes /
 // W.words: the room after the residual regions.  W.counts[0 .. nb] must be
 // zero already (the split's histogram kernel clears them).
-cudaError_t rowtile_pass_hashed(const Geo &G, uint32_t *cube, const Residual &R, uint64_t m, const BinWs &W,
-                                const cbaa_tuning &T, bool sampled, cudaStream_t s);
+cudaError_t rowtile_pass_residual(const Geo &G, uint32_t *cube, const Residual &R, uint64_t m, const BinWs &W,
+                                  const cbaa_tuning &T, bool sampled, cudaStream_t s);
 // Words a row-tile pass of m packets needs in the code buffer (sampled run
 // capacities with their overflow list, or exact counts).
 uint64_t rowtile_pass_words(const Geo &G, uint64_t m, bool sampled);

@@ -10,22 +10,27 @@
 // the head of a Zipf law), so:
 //
 //   1. k_heavy_sample : one tile of 1024 packets in 128 is counted by the top
-//                       15 bits of the mangled address (with the last
-//                       address seen in each slot)
+//                       15 bits of the source key (with a key seen in each
+//                       slot)
 //   2. k_heavy_hist, k_heavy_select : the most counted slots, up to K of
 //                       them, become the heavy sources; a lookup table maps a
-//                       mangled address to its heavy index (top 14 bits ->
-//                       low 18 bits as a tag and the index)
+//                       key to its heavy index (top 14 bits -> low 18 bits as
+//                       a tag and the index)
 //   3. k_heavy_split  : every packet: a heavy source's row bit is set in
 //                       its bitmap in shared memory (a bit already set is
 //                       only read); any other packet is written out as
-//                       {mangled ip, row}.  Each block ORs its bitmaps into
-//                       the global ones with one bulk reduction.
+//                       {iip, row}.  Each block ORs its bitmaps into the
+//                       global ones with one bulk reduction.
 //   4. k_heavy_expand : each heavy bitmap is ORed into the source's columns
 //   5. the row-tile pass over the residual entries (update_rowtile.cu)
 //
-// Which sources are heavy only decides the path a packet takes, never the
-// cube: every packet's bits are set by one of the two paths.
+// The source key is a multiplicative bijection of the inner address, not its
+// mangled form: one multiply instead of the mangle's five steps, and the
+// mangle is computed only for the residual packets (by the routing kernel)
+// and once per heavy source (by the expansion).  The row is computed for
+// every packet, once.  Which sources are heavy only
+// decides the path a packet takes, never the cube: every packet's bits are
+// set by one of the two paths.
 #include <cstring>
 
 #include "cbaa_internal.cuh"
@@ -60,7 +65,15 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
     asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-// Heavy index of mangled address m, or kHeavyIdxMask.  d = entry ^ (tag of
+// Source key of an inner address: x * an odd constant is a bijection of the
+// 32-bit words, and its top bits mix all bits of x (Knuth's multiplicative
+// hashing).  The expansion turns a key back into its address.
+constexpr uint32_t kHeavyKeyMul = 0x9E3779B1u;
+constexpr uint32_t kHeavyKeyInv = inv_odd(kHeavyKeyMul);
+static_assert(kHeavyKeyMul * kHeavyKeyInv == 1u, "inverse of the key multiplier");
+__device__ __forceinline__ uint32_t heavy_key(uint32_t ip) { return ip * kHeavyKeyMul; }
+
+// Heavy index of source key m, or kHeavyIdxMask.  d = entry ^ (tag of
 // m << kHeavyTabBits) keeps only the index field exactly when the tags agree,
 // and the empty marker's index field is all ones.
 __device__ __forceinline__ uint32_t heavy_index(const uint32_t *tab, uint32_t m) {
@@ -96,10 +109,10 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_heavy_sample(const Geo G,
         for (uint32_t u = 0; u < 4; ++u) {
             if (!have[u]) continue;
             if (ORIENT && !orient(G, v[u].x, v[u].y)) continue;
-            const uint32_t m = mangle(G, v[u].x);
+            const uint32_t m = heavy_key(v[u].x);
             const uint32_t slot = m >> (32 - kHeavyCountBits);
-            // the slot keeps an address seen at every 8th count of a block: a slot with
-            // one heavy source keeps that source's address with high probability
+            // the slot keeps a key seen at every 8th count of a block: a slot with
+            // one heavy source keeps that source's key with high probability
             if ((atomicAdd(&cnt[slot], 1u) & 7u) == 0u) key[slot] = m;
         }
     }
@@ -227,24 +240,23 @@ __device__ __forceinline__ uint32_t split_load(const uint32_t *pairs, uint64_t n
 }
 
 // The split of NP packets per lane of a warp (slot k of lane `lane`: a[k],
-// b[k], present when bit k of ok is set): hashes; lookups; bitmap words of
-// the heavy ones, read together; sets of the bits still clear; the others'
-// entries {mangled ip, row} written to `region` at places reserved with one
-// shared-memory atomic per warp.  In phases, so that the lanes' shared-memory
-// reads are in flight together.
+// b[k], present when bit k of ok is set): keys and rows; lookups; bitmap
+// words of the heavy ones, read together; sets of the bits still clear; the
+// others' entries {iip, row} (oriented) written to `region` at places
+// reserved with one shared-memory atomic per warp.  In phases, so that the lanes'
+// shared-memory reads are in flight together.
 template <uint32_t NP, bool ORIENT>
 __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab, uint32_t *bm, uint32_t (&a)[NP],
                                               uint32_t (&b)[NP], uint32_t ok, uint2 *region, uint32_t *s_cnt,
                                               uint32_t lane) {
-    uint32_t m[NP], row[NP], h[NP];
+    uint32_t row[NP], h[NP];
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
         if (ORIENT && ((ok >> k) & 1u) && !orient(G, a[k], b[k])) ok &= ~(1u << k);   // raw {src, dst} vs NI
-        m[k] = mangle(G, a[k]);
         row[k] = row_of(G, b[k]);
     }
 #pragma unroll
-    for (uint32_t k = 0; k < NP; ++k) h[k] = heavy_index(tab, m[k]);
+    for (uint32_t k = 0; k < NP; ++k) h[k] = heavy_index(tab, heavy_key(a[k]));
     uint32_t heavy = 0;
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
@@ -275,7 +287,7 @@ __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab,
     base = __shfl_sync(0xffffffffu, base, 31) + x - cnt;
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k)
-        if ((keep >> k) & 1u) region[base + __popc(keep & ((1u << k) - 1u))] = make_uint2(m[k], row[k]);
+        if ((keep >> k) & 1u) region[base + __popc(keep & ((1u << k) - 1u))] = make_uint2(a[k], row[k]);
 }
 
 // End of a split block: the region's count, then the block's bitmaps into the
@@ -312,7 +324,8 @@ __device__ __forceinline__ void split_prologue(const uint32_t *tab_g, uint32_t *
 
 // Every warp walks its own chunks of 256 packets (chunk c for c = global
 // warp, + all warps, ...), the next chunk's 16-byte loads in flight in
-// registers while it works on the current one.  Shared memory: the lookup
+// registers while it works on the current one (two register sets used in
+// turn, so nothing is copied between them).  Shared memory: the lookup
 // table, then K row bitmaps of W words (kwords words).  Residual entries go
 // to this block's region (rcap entries from blockIdx.x * rcap), one
 // shared-memory reservation per warp and chunk; the region's count is
@@ -365,7 +378,7 @@ __global__ void __launch_bounds__(256) k_heavy_expand(const Geo G, uint32_t *__r
     const uint32_t warps = gridDim.x * blockDim.x / 32;
     for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) / 32; t < nh * G.A; t += warps) {
         const uint32_t h = t / G.A, a = t - h * G.A;
-        const uint32_t m = list[h], cs = m & G.smask, lp = m >> G.r;
+        const uint32_t m = mangle(G, list[h] * kHeavyKeyInv), cs = m & G.smask, lp = m >> G.r;
         const uint32_t col = a < G.n_ra ? ra_col(G, a, lp) : va_col(G, a - G.n_ra, lp);
         uint32_t *dst = cube + (size_t)cs * G.cs_words + G.arr_base[a] + (size_t)col * G.W;
         const uint32_t *src = bits + (size_t)h * G.W;
@@ -456,7 +469,7 @@ cudaError_t heavy_pass(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint
     BinWs W2 = W;
     W2.codes = W.codes + rw;
     W2.words = W.words - rw;
-    return rowtile_pass_hashed(G, cube, R, m, W2, T, sampled, s);     // its counts were zeroed by k_heavy_hist
+    return rowtile_pass_residual(G, cube, R, m, W2, T, sampled, s);     // its counts were zeroed by k_heavy_hist
 }
 
 }  // namespace

@@ -109,12 +109,12 @@ __device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
 constexpr uint32_t kCountTile = 4 * kCountThreads;
 
 // ORIENT (the cube has an inner network): packets are raw {src, dst} (orient()).
-// HASHED: the input is the residual of the heavy split, entries {mangled
-// ip, row} already oriented, one segment of regions of rcap entries whose
-// first rcount[r] are valid (rcap a multiple of every tile and block size).
+// RESID: the input is the residual of the heavy split, entries {iip, row}
+// already oriented, one segment of regions of rcap entries whose first
+// rcount[r] are valid (rcap a multiple of every tile and block size).
 // samp > 1: only every samp-th tile of kCountTile packets is counted (a
 // sample for run capacities, see sample_capacity).
-template <bool MULTI, bool ORIENT, bool HASHED>
+template <bool MULTI, bool ORIENT, bool RESID>
 __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                             uint32_t *__restrict__ counts, uint32_t samp,
                                                             const uint32_t *__restrict__ rcount, uint64_t rcap) {
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
     __syncthreads();
     for (uint64_t base = lo; base < hi; base += step) {
         uint64_t thi = hi;                            // end of this tile's valid packets
-        if (HASHED) {
+        if (RESID) {
             const uint64_t r = base / rcap, ve = r * rcap + rcount[r];
             if (ve < thi) thi = ve;
             if (base >= thi) continue;
@@ -158,24 +158,18 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
             uint32_t ip[4] = {q0.x, q0.z, q1.x, q1.z}, oip[4] = {q0.y, q0.w, q1.y, q1.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (HASHED) {
-                    atomicAdd(&hist[rb + row_tile(G, 0, ip[u], oip[u])], 1u);
-                    continue;
-                }
-                if (ORIENT && !orient(G, ip[u], oip[u])) continue;      // raw {src, dst} against NI
-                atomicAdd(&hist[rb + row_tile(G, 0, mangle(G, ip[u]), row_of(G, oip[u]))], 1u);
+                if (!RESID && ORIENT && !orient(G, ip[u], oip[u])) continue;      // raw {src, dst} against NI
+                const uint32_t row = RESID ? oip[u] : row_of(G, oip[u]);
+                atomicAdd(&hist[rb + row_tile(G, 0, mangle(G, ip[u]), row)], 1u);
             }
         } else {
             const uint64_t end = base + kCountTile < thi ? base + kCountTile : thi;
             for (uint64_t p = base + threadIdx.x; p < end; p += kCountThreads) {
                 const uint32_t sp = seg_of(S, p);
                 uint2 v = ld_pair(S.pairs[sp] + 2 * (p - S.start[sp]));
-                if (HASHED) {
-                    atomicAdd(&hist[row_tile(G, B.unit(S, sp), v.x, v.y)], 1u);
-                    continue;
-                }
-                if (ORIENT && !orient(G, v.x, v.y)) continue;
-                atomicAdd(&hist[row_tile(G, B.unit(S, sp), mangle(G, v.x), row_of(G, v.y))], 1u);
+                if (!RESID && ORIENT && !orient(G, v.x, v.y)) continue;
+                const uint32_t row = RESID ? v.y : row_of(G, v.y);
+                atomicAdd(&hist[row_tile(G, B.unit(S, sp), mangle(G, v.x), row)], 1u);
             }
         }
     }
@@ -187,14 +181,14 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
 // SHORT records (r >= 5): lp << 5 | bit in 4 bytes; else {mangled ip, row}.
 // Shapes of up to 8 packets per thread are held to 32 registers (4-byte
 // records: 2048 threads per SM, measured ~8 % faster) or 42 (8-byte records).
-template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT, bool HASHED>
+template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT, bool RESID>
 __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) / THREADS) k_rt_scatter(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                         uint32_t *__restrict__ cursors, void *__restrict__ recs_out,
                                                         const uint32_t *__restrict__ offsets, uint2 *__restrict__ ovf,
                                                         uint32_t *__restrict__ ovf_count, uint32_t ovf_cap,
                                                         const uint32_t *__restrict__ rcount, uint64_t rcap) {
     extern __shared__ uint32_t sm[];
-    if (HASHED) {                                     // the valid part of this block's residual region
+    if (RESID) {                                     // the valid part of this block's residual region
         const uint64_t p0 = (uint64_t)blockIdx.x * THREADS * PPT, r = p0 / rcap, ve = r * rcap + rcount[r];
         if (ve < n) n = ve;
         if (p0 >= n) return;
@@ -252,9 +246,9 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
     for (uint32_t k = 0; k < PPT; ++k) {
         slot[k] = 0xFFFFFFFFu;
         if (rt[k] != 0xFFFFFFFFu) {
-            if (!HASHED && ORIENT && !orient(G, rec[k].x, rec[k].y)) continue;      // raw {src, dst} against NI
-            const uint32_t m = HASHED ? rec[k].x : mangle(G, rec[k].x);
-            const uint32_t row = HASHED ? rec[k].y : row_of(G, rec[k].y);
+            if (!RESID && ORIENT && !orient(G, rec[k].x, rec[k].y)) continue;      // raw {src, dst} against NI
+            const uint32_t m = mangle(G, rec[k].x);
+            const uint32_t row = RESID ? rec[k].y : row_of(G, rec[k].y);
             const uint32_t b = row_tile(G, rt[k], m, row);
             if (SHORT) rec[k].x = ((m >> G.r) << 5) | (row & 31u);
             else rec[k] = make_uint2(m, row);
@@ -634,14 +628,14 @@ uint32_t routing_table_tiles(const Geo &G, const BinSegs &S, uint32_t nb, uint64
     return span_max * tpr < nb ? (uint32_t)(span_max * tpr) : nb;
 }
 
-template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT, bool HASHED>
+template <int THREADS, int PPT, bool SHORT, bool MULTI, bool ORIENT, bool RESID>
 cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                               const Overflow &O, const uint32_t *rcount, uint64_t rcap, cudaStream_t s) {
     // several cubes: every block numbers its own tiles within tables of nbt entries
     const uint32_t nbt = MULTI ? routing_table_tiles(G, S, nb, (uint64_t)THREADS * PPT) : nb;
     const size_t per = SHORT ? 2 : 3;                 // staged record words + bin word per packet
     const size_t smem = sizeof(uint32_t) * (((3 * (size_t)nbt + 1) & ~(size_t)1) + per * THREADS * PPT);
-    auto k = k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT, HASHED>;
+    auto k = k_rt_scatter<THREADS, PPT, SHORT, MULTI, ORIENT, RESID>;
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((m + THREADS * PPT - 1) / (THREADS * PPT));
@@ -650,27 +644,27 @@ cudaError_t launch_rt_scatter(const Geo &G, const BinSegs &S, uint64_t m, uint32
     return cudaGetLastError();
 }
 
-template <bool SHORT, bool MULTI, bool ORIENT, bool HASHED>
+template <bool SHORT, bool MULTI, bool ORIENT, bool RESID>
 cudaError_t launch_rt_scatter_shape(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                                     const Overflow &O, uint32_t shape, const uint32_t *rcount, uint64_t rcap,
                                     cudaStream_t s) {
     switch (shape) {
-        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
-        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
-        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
-        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
-        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
-        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
-        case 7: return launch_rt_scatter<256, 16, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 1: return launch_rt_scatter<512, 4, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 2: return launch_rt_scatter<1024, 4, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 3: return launch_rt_scatter<256, 8, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 4: return launch_rt_scatter<256, 4, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 5: return launch_rt_scatter<1024, 8, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 6: return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
+        case 7: return launch_rt_scatter<256, 16, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
         case 8: {
             // 1024 x 16 stages 16Ki records: with 8-byte records or many tiles it exceeds shared memory
             const uint32_t nbt = MULTI ? routing_table_tiles(G, S, nb, 16384) : nb;
             const size_t need = sizeof(uint32_t) * ((((size_t)3 * nbt + 1) & ~(size_t)1) + (SHORT ? 2 : 3) * 16384);
             if (need + 1024 > 227u * 1024u)
-                return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
-            return launch_rt_scatter<1024, 16, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+                return launch_rt_scatter<512, 16, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
+            return launch_rt_scatter<1024, 16, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
         }
-        default: return launch_rt_scatter<512, 8, SHORT, MULTI, ORIENT, HASHED>(G, S, m, nb, W, O, rcount, rcap, s);
+        default: return launch_rt_scatter<512, 8, SHORT, MULTI, ORIENT, RESID>(G, S, m, nb, W, O, rcount, rcap, s);
     }
 }
 
@@ -746,10 +740,10 @@ static uint64_t sampled_pass_max(const BinWs &W, uint32_t nb, uint64_t rec_words
     return lo;
 }
 
-// One pass over m packets (HASHED: the residual regions R, m entries at most,
+// One pass over m packets (RESID: the residual regions R, m entries at most,
 // the input spans R->nreg * R->rcap positions): counts (or sampled
 // capacities), scan, routing, assembly.
-template <bool MULTI, bool ORIENT, bool HASHED>
+template <bool MULTI, bool ORIENT, bool RESID>
 static cudaError_t rowtile_pass(const Geo &G, const BinSegs &S, uint64_t m, uint32_t nb, const BinWs &W,
                                 const cbaa_tuning &T, bool sampled, const Residual *R, cudaStream_t s) {
     const uint32_t tw = rowtile_words(G);
@@ -760,14 +754,14 @@ static cudaError_t rowtile_pass(const Geo &G, const BinSegs &S, uint64_t m, uint
     const uint32_t count_bps = T.count_blocks_per_sm ? T.count_blocks_per_sm : 8;
     const uint32_t apply_ips = T.apply_items_per_sm ? T.apply_items_per_sm : 8;
     const uint32_t samp = sampled ? kSample : 1u;
-    auto kcount = k_rt_count<MULTI, ORIENT, HASHED>;
+    auto kcount = k_rt_count<MULTI, ORIENT, RESID>;
     cudaError_t e;
     if ((e = allow_smem(kcount, sizeof(uint32_t) * nb)) != cudaSuccess) return e;
     // counts[nb] is the overflow counter of a sampled pass (a residual pass finds them zeroed by the split)
-    if (!HASHED && (e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * (nb + 1), s)) != cudaSuccess) return e;
-    const uint64_t span = HASHED ? (uint64_t)R->nreg * R->rcap : m;      // positions the kernels walk
-    const uint32_t *rcount = HASHED ? R->rcount : nullptr;
-    const uint64_t rcap = HASHED ? R->rcap : 1;
+    if (!RESID && (e = cudaMemsetAsync(W.counts, 0, sizeof(uint32_t) * (nb + 1), s)) != cudaSuccess) return e;
+    const uint64_t span = RESID ? (uint64_t)R->nreg * R->rcap : m;      // positions the kernels walk
+    const uint32_t *rcount = RESID ? R->rcount : nullptr;
+    const uint64_t rcap = RESID ? R->rcap : 1;
     const uint64_t want = (span + (uint64_t)kCountTile * samp - 1) / ((uint64_t)kCountTile * samp);
     const uint64_t cap = (uint64_t)sms * count_bps;
     const unsigned cgrid = (unsigned)(want < cap ? want : cap);
@@ -782,7 +776,7 @@ static cudaError_t rowtile_pass(const Geo &G, const BinSegs &S, uint64_t m, uint
         const uint64_t rec_region = (rec_words * sample_capacity_bound(m, nb, kSample, kCountTile) + 3) & ~3ull;
         O = Overflow{reinterpret_cast<uint2 *>(W.codes + rec_region), W.counts + nb, (uint32_t)m};
     }
-    if (HASHED)
+    if (RESID)
         e = short_rec ? launch_rt_scatter_shape<true, false, false, true>(G, S, span, nb, W, O, T.scatter_shape, rcount,
                                                                           rcap, s)
                       : launch_rt_scatter_shape<false, false, false, true>(G, S, span, nb, W, O, T.scatter_shape,
@@ -790,7 +784,7 @@ static cudaError_t rowtile_pass(const Geo &G, const BinSegs &S, uint64_t m, uint
     else
         e = launch_rt_scatter_kind<MULTI, ORIENT>(G, S, m, nb, W, O, T.scatter_shape, s);
     if (e != cudaSuccess) return e;
-    if (HASHED && pair_ok(G))                         // residual tiles are of similar size: whole pairs
+    if (RESID && pair_ok(G))                         // residual tiles are of similar size: whole pairs
         return short_rec ? launch_rt_apply_pair<uint32_t>(G, S, W, nb, tw, sms, O.list, O.count, O.cap, s)
                          : launch_rt_apply_pair<uint2>(G, S, W, nb, tw, sms, O.list, O.count, O.cap, s);
     return short_rec ? launch_rt_apply<uint32_t>(G, S, W, nb, (uint32_t)ch, tw, apply_smem, sms, O.list, O.count,
@@ -799,8 +793,8 @@ static cudaError_t rowtile_pass(const Geo &G, const BinSegs &S, uint64_t m, uint
                                               s);
 }
 
-cudaError_t rowtile_pass_hashed(const Geo &G, uint32_t *cube, const Residual &R, uint64_t m, const BinWs &W,
-                                const cbaa_tuning &T, bool sampled, cudaStream_t s) {
+cudaError_t rowtile_pass_residual(const Geo &G, uint32_t *cube, const Residual &R, uint64_t m, const BinWs &W,
+                                  const cbaa_tuning &T, bool sampled, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     BinSegs S;
     memset(&S, 0, sizeof S);
