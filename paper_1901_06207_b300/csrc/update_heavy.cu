@@ -73,14 +73,6 @@ constexpr uint32_t kHeavyKeyInv = inv_odd(kHeavyKeyMul);
 static_assert(kHeavyKeyMul * kHeavyKeyInv == 1u, "inverse of the key multiplier");
 __device__ __forceinline__ uint32_t heavy_key(uint32_t ip) { return ip * kHeavyKeyMul; }
 
-// Heavy index of source key m, or kHeavyIdxMask.  d = entry ^ (tag of
-// m << kHeavyTabBits) keeps only the index field exactly when the tags agree,
-// and the empty marker's index field is all ones.
-__device__ __forceinline__ uint32_t heavy_index(const uint32_t *tab, uint32_t m) {
-    const uint32_t d = tab[m >> kHeavyTagBits] ^ ((m & kTagMask) << kHeavyTabBits);
-    return d < kHeavyIdxMask ? d : kHeavyIdxMask;
-}
-
 // Counts of the sample by slot, first in shared memory (one table per
 // block, 2^15 counters), then added to the global table: a heavy source's
 // slot gets one global atomic per block instead of one per sampled packet.
@@ -210,12 +202,13 @@ __device__ __forceinline__ uint32_t heavy_count(const uint32_t *ctr, uint32_t km
 // Packets of chunk c (32 lanes x 8 packets, 2 per 16-byte load) into q;
 // ok: bit k set when slot k of this lane holds a packet.  Slot 2j + h of lane
 // l is packet c * 256 + 2 (l + 32 j) + h.
-__device__ __forceinline__ uint32_t split_load(const uint32_t *pairs, uint64_t n, uint64_t c, uint32_t lane,
-                                               bool al, uint4 (&q)[4]) {
-    const uint64_t c0 = c * 256;
-    if (al && c0 + 256 <= n) {
+__device__ __forceinline__ uint32_t split_load(const uint32_t *pairs, uint64_t n, uint32_t c, uint32_t lane,
+                                               uint32_t full, uint4 (&q)[4]) {
+    const uint64_t c0 = (uint64_t)c * 256;
+    if (c < full) {                                   // a whole chunk at a 16-byte aligned address
+        const uint32_t *p = pairs + 2 * c0 + 4 * lane;
 #pragma unroll
-        for (uint32_t j = 0; j < 4; ++j) q[j] = ld_quad_nc(pairs + 2 * c0 + 4 * (lane + 32 * j));
+        for (uint32_t j = 0; j < 4; ++j) q[j] = ld_quad_nc(p + 128 * j);
         return 0xFFu;
     }
     uint32_t ok = 0;
@@ -239,40 +232,55 @@ __device__ __forceinline__ uint32_t split_load(const uint32_t *pairs, uint64_t n
     return ok;
 }
 
+// Shared-memory OR of `bit` into the word at shared address `sa` when `p`;
+// predicated, so that no branch surrounds it.
+__device__ __forceinline__ void red_or_shared_if(uint32_t sa, uint32_t bit, uint32_t p) {
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q red.shared.or.b32 [%0], %1; }"
+                 :: "r"(sa), "r"(bit), "r"(p) : "memory");
+}
+
+// 8-byte store of {x, y} to `ptr` when `p` (predicated).
+__device__ __forceinline__ void st_pair_if(uint2 *ptr, uint32_t x, uint32_t y, uint32_t p) {
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q st.global.v2.u32 [%0], {%1, %2}; }"
+                 :: "l"(ptr), "r"(x), "r"(y), "r"(p) : "memory");
+}
+
 // The split of NP packets per lane of a warp (slot k of lane `lane`: a[k],
-// b[k], present when bit k of ok is set): keys and rows; lookups; bitmap
-// words of the heavy ones, read together; sets of the bits still clear; the
-// others' entries {iip, row} (oriented) written to `region` at places
-// reserved with one shared-memory atomic per warp.  In phases, so that the lanes'
-// shared-memory reads are in flight together.
+// b[k], present when bit k of ok is set): rows and lookups; bitmap words of
+// the heavy ones (word 0 for the others), read together; sets of the bits
+// still clear; the others' entries {iip, row} (oriented) written to `region`
+// at places reserved with one shared-memory atomic per warp.  In phases, so
+// that the lanes' shared-memory reads are in flight together, and without
+// branches: the sets and the stores are predicated.  bm_s: the shared
+// address of bm.
 template <uint32_t NP, bool ORIENT>
-__device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab, uint32_t *bm, uint32_t (&a)[NP],
-                                              uint32_t (&b)[NP], uint32_t ok, uint2 *region, uint32_t *s_cnt,
-                                              uint32_t lane) {
-    uint32_t row[NP], h[NP];
+__device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab, const uint32_t *bm, uint32_t bm_s,
+                                              uint32_t (&a)[NP], uint32_t (&b)[NP], uint32_t ok, uint2 *region,
+                                              uint32_t *s_cnt, uint32_t lane) {
+    uint32_t row[NP], e[NP];
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
         if (ORIENT && ((ok >> k) & 1u) && !orient(G, a[k], b[k])) ok &= ~(1u << k);   // raw {src, dst} vs NI
         row[k] = row_of(G, b[k]);
+        e[k] = tab[heavy_key(a[k]) >> kHeavyTagBits];
     }
-#pragma unroll
-    for (uint32_t k = 0; k < NP; ++k) h[k] = heavy_index(tab, heavy_key(a[k]));
-    uint32_t heavy = 0;
+    // e ^ (key << 14) keeps only the index field exactly when the tags agree
+    // (key << 14 == a * (mul << 14) modulo 2^32); the empty marker's index
+    // field is all ones
+    uint32_t heavy = 0, wi[NP], wv[NP];
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
-        if (((ok >> k) & 1u) && h[k] < kHeavyIdxMask) {
-            heavy |= 1u << k;
-            h[k] = h[k] * G.W + (row[k] >> 5);                // the bitmap word
-        }
+        const uint32_t d = e[k] ^ (a[k] * (kHeavyKeyMul << kHeavyTabBits));
+        const bool hv = ((ok >> k) & 1u) && d < kHeavyIdxMask;
+        heavy |= (uint32_t)hv << k;
+        wi[k] = hv ? d * G.W + (row[k] >> 5) : 0u;                // the bitmap word (word 0: not heavy)
+        wv[k] = bm[wi[k]];
     }
-    uint32_t wv[NP];
-#pragma unroll
-    for (uint32_t k = 0; k < NP; ++k) wv[k] = ((heavy >> k) & 1u) ? bm[h[k]] : 0xFFFFFFFFu;
     // a stale read only costs an atomic that changes nothing: every set is an OR
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
-        const uint32_t bit = 1u << (row[k] & 31u);
-        if (!(wv[k] & bit)) atomicOr(&bm[h[k]], bit);
+        const uint32_t bit = __funnelshift_l(0u, 1u, row[k]);      // 1 << (row & 31)
+        red_or_shared_if(bm_s + 4u * wi[k], bit, ((heavy >> k) & 1u) & (uint32_t)!(wv[k] & bit));
     }
     const uint32_t keep = ok & ~heavy;
     const uint32_t cnt = __popc(keep);
@@ -285,9 +293,13 @@ __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab,
     uint32_t base = 0;
     if (lane == 31 && x) base = atomicAdd(s_cnt, x);
     base = __shfl_sync(0xffffffffu, base, 31) + x - cnt;
+    uint2 *out = region + base;                                // this lane's entries, in slot order
 #pragma unroll
-    for (uint32_t k = 0; k < NP; ++k)
-        if ((keep >> k) & 1u) region[base + __popc(keep & ((1u << k) - 1u))] = make_uint2(a[k], row[k]);
+    for (uint32_t k = 0; k < NP; ++k) {
+        const uint32_t kk = (keep >> k) & 1u;
+        st_pair_if(out, a[k], row[k], kk);
+        out += kk;
+    }
 }
 
 // End of a split block: the region's count, then the block's bitmaps into the
@@ -345,21 +357,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
     if (tid == 0) s_cnt = 0;
     __syncthreads();
     uint2 *region = resid + (uint64_t)blockIdx.x * rcap;
-    const bool al = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
-    const uint64_t chunks = (n + 255) / 256;
-    const uint64_t nw = (uint64_t)gridDim.x * (THREADS / 32);
-    uint64_t c = (uint64_t)blockIdx.x * (THREADS / 32) + (tid >> 5);
+    const uint32_t bm_s = static_cast<uint32_t>(__cvta_generic_to_shared(bm));
+    // chunk numbers fit 32 bits: a pass holds far fewer than 2^40 packets
+    const uint32_t chunks = (uint32_t)((n + 255) / 256);
+    const uint32_t full = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0 ? (uint32_t)(n / 256) : 0u;
+    const uint32_t nw = gridDim.x * (THREADS / 32);
+    uint32_t c = blockIdx.x * (THREADS / 32) + (tid >> 5);
     uint4 q[4], qn[4];
-    uint32_t ok = c < chunks ? split_load(pairs, n, c, lane, al, q) : 0u;
+    uint32_t ok = c < chunks ? split_load(pairs, n, c, lane, full, q) : 0u;
     for (; c < chunks; c += nw) {
-        const uint32_t okn = c + nw < chunks ? split_load(pairs, n, c + nw, lane, al, qn) : 0u;
+        const uint32_t okn = c + nw < chunks ? split_load(pairs, n, c + nw, lane, full, qn) : 0u;
         uint32_t a[8], b[8];
 #pragma unroll
         for (uint32_t k = 0; k < 8; ++k) {
             a[k] = (k & 1u) ? q[k / 2].z : q[k / 2].x;
             b[k] = (k & 1u) ? q[k / 2].w : q[k / 2].y;
         }
-        split_packets<8, ORIENT>(G, tab, bm, a, b, ok, region, &s_cnt, lane);
+        split_packets<8, ORIENT>(G, tab, bm, bm_s, a, b, ok, region, &s_cnt, lane);
 #pragma unroll
         for (uint32_t j = 0; j < 4; ++j) q[j] = qn[j];
         ok = okn;
