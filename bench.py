@@ -299,6 +299,44 @@ def load_traffic(workload_name: str, path: str):
     return d.get("dram_bytes_per_launch")
 
 
+def detect_only(args, C, cube, ws, out, info, theta, stream, hosts):
+    """The window's detect alone on its cube, the packets freed by the caller: a full-size detect
+    with a device footprint of one cube and one workspace (for profiling the detect kernels)."""
+    import torch
+    torch.cuda.empty_cache()
+    ms = []
+    for _ in range(max(args.steps, 1)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cube.detect_async(theta, ws, out, info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    h2, inf = C.hosts_from_device(out, info)
+    assert inf["status"] == C.OK and np.array_equal(h2["ip"], hosts["ip"]), inf
+    g = cube.geometry
+    n_arr = g["n_ra"] + g["n_va"]
+    zc_t = torch.empty((1 << g["r"]) * n_arr * max(1 << c for c in g["cbn"][:n_arr]), dtype=torch.int16,
+                       device=stream.device)
+    za_t = torch.empty(1 << g["r"], n_arr, dtype=torch.int64, device=stream.device)
+    eps_t = torch.empty(1 << g["r"], dtype=torch.float64, device=stream.device)
+    zmax_t = torch.empty(1 << g["r"], dtype=torch.int64, device=stream.device)
+    zc_ms = []
+    for _ in range(max(args.steps, 1)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = C.lib().cbaa_column_stats(cube.handle, theta, zc_t.data_ptr(), za_t.data_ptr(), eps_t.data_ptr(),
+                                       zmax_t.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        assert st == 0, st
+        torch.cuda.synchronize()
+        zc_ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"detect_only": True, "hosts": int(h2.size), "detect_ms_p50": float(np.median(ms)),
+                      "column_stats_ms_p50": float(np.median(zc_ms)),
+                      "device_bytes": int(torch.cuda.memory_allocated())}))
+    return 0
+
+
 def run_cbaa(args):
     import torch
     from paper_1901_06207_b300 import cbaa as C
@@ -392,6 +430,10 @@ def run_cbaa(args):
     torch.cuda.synchronize()
     hosts, inf = C.hosts_from_device(out, info)
     assert inf["status"] == C.OK, inf
+    if args.detect_only:
+        pairs_dev = pairs_pin = uws = None            # the packets and the second buffers freed
+        cubes2[1] = ws2[1] = out2[1] = info2[1] = None
+        return detect_only(args, C, cube, ws, out, info, theta, stream, hosts)
 
     # L2 RED.OR roof on a buffer the size of the cube (the update kernel's bound)
     red_buf = torch.empty(cube.nbytes // 4, dtype=torch.int32, device=dev)
@@ -1143,6 +1185,9 @@ def main():
                          "fewer than a window makes the update run in several passes")
     ap.add_argument("--scale-shift", type=int, default=0,
                     help="window64m: the same window shape at 2^-k the packets and pool (small profiling cases)")
+    ap.add_argument("--detect-only", action="store_true",
+                    help="window workloads: after the warm-up, free the packets and time the detect alone "
+                         "(a full-size detect in a small device footprint, for profiling)")
     ap.add_argument("--learned-size", default="full", choices=["full", "scaled"],
                     help="learned workload: 256M-packet windows (full) or 64M with the same column load")
     args = ap.parse_args()
