@@ -53,13 +53,14 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 // result: the last step XORs x >> 16 into bits 0..15 and leaves bits 16..31
 // as they are, so mix32(x) >> s == mix32_top(x) >> s for every s >= 16.  The
 // row hash keeps the top log2 g <= 15 bits and the VA hash the top cbn <= 16.
-__host__ __device__ __forceinline__ uint32_t mix32_top(uint32_t x) {
-    x ^= x >> 16;
+// The steps of mix32 after its first one (x ^= x >> 16), without the last.
+__host__ __device__ __forceinline__ uint32_t mix32_mid(uint32_t x) {
     x *= 0x7feb352du;
     x ^= x >> 15;
     x *= 0x846ca68bu;
     return x;
 }
+__host__ __device__ __forceinline__ uint32_t mix32_top(uint32_t x) { return mix32_mid(x ^ (x >> 16)); }
 
 // Inverse multipliers modulo 2^32 (a * a^-1 == 1), fixed at compile time by
 // Newton's iteration on the host compiler.

@@ -65,6 +65,14 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
     asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
+// H_bv(oip) with its seed folded in: the finaliser's first step applied to
+// oip ^ s is (oip ^ (oip >> 16)) ^ (s ^ (s >> 16)), so with seed_fold =
+// s ^ (s >> 16) computed once the seed costs no instruction of its own.
+// Equal to row_of(G, oip).
+__device__ __forceinline__ uint32_t row_of_folded(const Geo &G, uint32_t oip, uint32_t seed_fold) {
+    return mix32_mid(oip ^ (oip >> 16) ^ seed_fold) >> (32u - G.log2_g);
+}
+
 // Source key of an inner address: x * an odd constant is a bijection of the
 // 32-bit words, and its top bits mix all bits of x (Knuth's multiplicative
 // hashing).  The expansion turns a key back into its address.
@@ -247,21 +255,23 @@ __device__ __forceinline__ void st_pair_if(uint2 *ptr, uint32_t x, uint32_t y, u
 
 // The split of NP packets per lane of a warp (slot k of lane `lane`: a[k],
 // b[k], present when bit k of ok is set): rows and lookups; bitmap words of
-// the heavy ones (word 0 for the others), read together; sets of the bits
+// the heavy ones (some word for the others), read together; sets of the bits
 // still clear; the others' entries {iip, row} (oriented) written to `region`
 // at places reserved with one shared-memory atomic per warp.  In phases, so
 // that the lanes' shared-memory reads are in flight together, and without
 // branches: the sets and the stores are predicated.  bm_s: the shared
-// address of bm.
+// address of bm; kmask: heavy sources in bm - 1 (a power of two less one);
+// seed_fold: the row hash's seed folded for row_of_folded.
 template <uint32_t NP, bool ORIENT>
 __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab, const uint32_t *bm, uint32_t bm_s,
-                                              uint32_t (&a)[NP], uint32_t (&b)[NP], uint32_t ok, uint2 *region,
-                                              uint32_t *s_cnt, uint32_t lane) {
+                                              uint32_t kmask, uint32_t seed_fold, uint32_t (&a)[NP],
+                                              uint32_t (&b)[NP], uint32_t ok, uint2 *region, uint32_t *s_cnt,
+                                              uint32_t lane) {
     uint32_t row[NP], e[NP];
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
         if (ORIENT && ((ok >> k) & 1u) && !orient(G, a[k], b[k])) ok &= ~(1u << k);   // raw {src, dst} vs NI
-        row[k] = row_of(G, b[k]);
+        row[k] = row_of_folded(G, b[k], seed_fold);
         e[k] = tab[heavy_key(a[k]) >> kHeavyTagBits];
     }
     // e ^ (key << 14) keeps only the index field exactly when the tags agree
@@ -273,7 +283,9 @@ __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab,
         const uint32_t d = e[k] ^ (a[k] * (kHeavyKeyMul << kHeavyTabBits));
         const bool hv = ((ok >> k) & 1u) && d < kHeavyIdxMask;
         heavy |= (uint32_t)hv << k;
-        wi[k] = hv ? d * G.W + (row[k] >> 5) : 0u;                // the bitmap word (word 0: not heavy)
+        // the bitmap word; for a packet that is not heavy some source's word (d & kmask
+        // < K), read and never set
+        wi[k] = (d & kmask) * G.W + (row[k] >> 5);
         wv[k] = bm[wi[k]];
     }
     // a stale read only costs an atomic that changes nothing: every set is an OR
@@ -358,6 +370,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
     __syncthreads();
     uint2 *region = resid + (uint64_t)blockIdx.x * rcap;
     const uint32_t bm_s = static_cast<uint32_t>(__cvta_generic_to_shared(bm));
+    const uint32_t kmask = kwords / G.W - 1u;          // heavy sources held: a power of two
+    const uint32_t seed_fold = G.seed_bv ^ (G.seed_bv >> 16);
     // chunk numbers fit 32 bits: a pass holds far fewer than 2^40 packets
     const uint32_t chunks = (uint32_t)((n + 255) / 256);
     const uint32_t full = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0 ? (uint32_t)(n / 256) : 0u;
@@ -373,7 +387,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
             a[k] = (k & 1u) ? q[k / 2].z : q[k / 2].x;
             b[k] = (k & 1u) ? q[k / 2].w : q[k / 2].y;
         }
-        split_packets<8, ORIENT>(G, tab, bm, bm_s, a, b, ok, region, &s_cnt, lane);
+        split_packets<8, ORIENT>(G, tab, bm, bm_s, kmask, seed_fold, a, b, ok, region, &s_cnt, lane);
 #pragma unroll
         for (uint32_t j = 0; j < 4; ++j) q[j] = qn[j];
         ok = okn;
