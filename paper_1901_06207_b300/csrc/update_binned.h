@@ -162,11 +162,59 @@ cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S, uint64_t n, co
 // Residual of the heavy split: region b holds rcount[b] entries {mangled
 // ip, row} from entry b * rcap on (rcap a multiple of kHeavyRegionAlign),
 // nreg regions.
+// Source key of an inner address, by which the heavy split looks sources up:
+// x * an odd constant is a bijection of the 32-bit words, and its top bits mix
+// all bits of x (Knuth's multiplicative hashing).  The expansion turns a key
+// back into its address.
+constexpr uint32_t kHeavyKeyMul = 0x9E3779B1u;
+constexpr uint32_t kHeavyKeyInv = inv_odd(kHeavyKeyMul);
+static_assert(kHeavyKeyMul * kHeavyKeyInv == 1u, "inverse of the key multiplier");
+__host__ __device__ __forceinline__ uint32_t heavy_key(uint32_t ip) { return ip * kHeavyKeyMul; }
+
+// The heavy sources of a split pass, whose row bitmaps the residual's
+// counting kernel ORs into their columns (list null: nothing to expand).
+struct HeavyExpand {
+    const uint32_t *list;          // key of heavy source h
+    const uint32_t *ctr;           // [0], [1]: sources taken (see k_heavy_select)
+    const uint32_t *bits;          // row bitmaps, W words per source
+    uint32_t kmax;
+};
+
+// Heavy sources taken: the upper ones plus the lower ones that found room.
+__host__ __device__ __forceinline__ uint32_t heavy_count(const uint32_t *ctr, uint32_t kmax) {
+    const uint32_t t = ctr[0] + ctr[1];
+    return t < kmax ? t : kmax;
+}
+
+#ifdef __CUDACC__
+// Part `part` of `parts` equal parts (blocks of whole warps) of the
+// expansion: one warp per (heavy source, array), the source's row bitmap ORed
+// into its column of that array, one reduction per non-zero word.
+__device__ __forceinline__ void heavy_expand_part(const Geo &G, uint32_t *cube, const HeavyExpand &X, uint32_t part,
+                                                  uint32_t parts) {
+    const uint32_t nh = heavy_count(X.ctr, X.kmax);
+    const uint32_t lane = threadIdx.x & 31u, wpb = blockDim.x / 32;
+    const uint32_t warps = parts * wpb;
+    for (uint32_t t = part * wpb + threadIdx.x / 32; t < nh * G.A; t += warps) {
+        const uint32_t h = t / G.A, a = t - h * G.A;
+        const uint32_t m = mangle(G, X.list[h] * kHeavyKeyInv), cs = m & G.smask, lp = m >> G.r;
+        const uint32_t col = a < G.n_ra ? ra_col(G, a, lp) : va_col(G, a - G.n_ra, lp);
+        uint32_t *dst = cube + (size_t)cs * G.cs_words + G.arr_base[a] + (size_t)col * G.W;
+        const uint32_t *src = X.bits + (size_t)h * G.W;
+        for (uint32_t w = lane; w < G.W; w += 32) {
+            const uint32_t x = src[w];
+            if (x) asm volatile("red.global.or.b32 [%0], %1;" :: "l"(dst + w), "r"(x) : "memory");
+        }
+    }
+}
+#endif
+
 struct Residual {
     const uint2 *entries;
     const uint32_t *rcount;
     uint64_t rcap;
     uint32_t nreg;
+    HeavyExpand x;                 // done by the residual pass's counting kernel
 };
 // One row-tile pass over the residual entries of the heavy split (m of them
 // at most), with run capacities from a sample when `sampled`; W.codes /

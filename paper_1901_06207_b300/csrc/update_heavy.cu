@@ -21,8 +21,9 @@
 //                       only read); any other packet is written out as
 //                       {iip, row}.  Each block ORs its bitmaps into the
 //                       global ones with one bulk reduction.
-//   4. k_heavy_expand : each heavy bitmap is ORed into the source's columns
-//   5. the row-tile pass over the residual entries (update_rowtile.cu)
+//   4. the row-tile pass over the residual entries (update_rowtile.cu), whose
+//      counting kernel also ORs each heavy bitmap into the source's columns
+//      (extra blocks: a launch fewer)
 //
 // The source key is a multiplicative bijection of the inner address, not its
 // mangled form: one multiply instead of the mangle's five steps, and the
@@ -61,9 +62,6 @@ __device__ __forceinline__ uint2 ld_pair_nc(const uint32_t *p) {
     return v;
 }
 
-__device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
-    asm volatile("red.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
-}
 
 // H_bv(oip) with its seed folded in: the finaliser's first step applied to
 // oip ^ s is (oip ^ (oip >> 16)) ^ (s ^ (s >> 16)), so with seed_fold =
@@ -73,13 +71,6 @@ __device__ __forceinline__ uint32_t row_of_folded(const Geo &G, uint32_t oip, ui
     return mix32_mid(oip ^ (oip >> 16) ^ seed_fold) >> (32u - G.log2_g);
 }
 
-// Source key of an inner address: x * an odd constant is a bijection of the
-// 32-bit words, and its top bits mix all bits of x (Knuth's multiplicative
-// hashing).  The expansion turns a key back into its address.
-constexpr uint32_t kHeavyKeyMul = 0x9E3779B1u;
-constexpr uint32_t kHeavyKeyInv = inv_odd(kHeavyKeyMul);
-static_assert(kHeavyKeyMul * kHeavyKeyInv == 1u, "inverse of the key multiplier");
-__device__ __forceinline__ uint32_t heavy_key(uint32_t ip) { return ip * kHeavyKeyMul; }
 
 // Counts of the sample by slot, first in shared memory (one table per
 // block, 2^15 counters), then added to the global table: a heavy source's
@@ -199,12 +190,6 @@ __global__ void __launch_bounds__(1024) k_heavy_select(const uint32_t *__restric
     const uint32_t k = __ldcg(key + i);
     list[h] = k;
     atomicCAS(&tab[k >> kHeavyTagBits], kHeavyEmpty, ((k & kTagMask) << kHeavyTabBits) | h);
-}
-
-// Heavy sources taken: the upper ones plus the lower ones that found room.
-__device__ __forceinline__ uint32_t heavy_count(const uint32_t *ctr, uint32_t kmax) {
-    const uint32_t t = ctr[0] + ctr[1];
-    return t < kmax ? t : kmax;
 }
 
 // Packets of chunk c (32 lanes x 8 packets, 2 per 16-byte load) into q;
@@ -395,28 +380,6 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
     split_flush(bm, kwords, bits_g, &s_cnt, rcount);
 }
 
-// One warp per (heavy source, array): the source's row bitmap ORed into its
-// column of that array.
-__global__ void __launch_bounds__(256) k_heavy_expand(const Geo G, uint32_t *__restrict__ cube,
-                                                      const uint32_t *__restrict__ list,
-                                                      const uint32_t *__restrict__ ctr, uint32_t kmax,
-                                                      const uint32_t *__restrict__ bits) {
-    const uint32_t nh = heavy_count(ctr, kmax);
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t warps = gridDim.x * blockDim.x / 32;
-    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) / 32; t < nh * G.A; t += warps) {
-        const uint32_t h = t / G.A, a = t - h * G.A;
-        const uint32_t m = mangle(G, list[h] * kHeavyKeyInv), cs = m & G.smask, lp = m >> G.r;
-        const uint32_t col = a < G.n_ra ? ra_col(G, a, lp) : va_col(G, a - G.n_ra, lp);
-        uint32_t *dst = cube + (size_t)cs * G.cs_words + G.arr_base[a] + (size_t)col * G.W;
-        const uint32_t *src = bits + (size_t)h * G.W;
-        for (uint32_t w = lane; w < G.W; w += 32) {
-            const uint32_t x = src[w];
-            if (x) red_or(dst + w, x);
-        }
-    }
-}
-
 uint32_t heavy_budget(const cbaa_tuning &T) { return T.heavy == 2 ? (64u << 10) : kHeavyBitmapMax; }
 
 // Heavy sources that fit the bitmap budget (W words each), at most kHeavyMax.
@@ -447,7 +410,8 @@ Residual residual_layout(const cbaa_tuning &T, uint64_t m, const uint32_t *entri
     const uint64_t nw = blocks * wpb;
     const uint64_t per_warp = (chunks + nw - 1) / nw;
     const uint64_t rcap = (wpb * per_warp * 256 + kHeavyRegionAlign - 1) / kHeavyRegionAlign * kHeavyRegionAlign;
-    return Residual{reinterpret_cast<const uint2 *>(entries_base), rcount, rcap, (uint32_t)blocks};
+    return Residual{reinterpret_cast<const uint2 *>(entries_base), rcount, rcap, (uint32_t)blocks,
+                    HeavyExpand{nullptr, nullptr, nullptr, 0}};
 }
 
 template <uint32_t THREADS, uint32_t MINB, bool ORIENT>
@@ -483,15 +447,10 @@ cudaError_t heavy_pass(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint
     k_heavy_select<<<kCountSlots / 1024, 1024, 0, s>>>(W.heavy.count, W.heavy.key, K, W.heavy.tab, W.heavy.list,
                                                       W.heavy.ctr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const Residual R = residual_layout(T, m, W.codes, W.heavy.rcount());
+    Residual R = residual_layout(T, m, W.codes, W.heavy.rcount());
+    R.x = HeavyExpand{W.heavy.list, W.heavy.ctr, W.heavy.bits, K};
     e = launch_split<1024, 1, ORIENT>(G, pairs, m, W, kwords, R, s);
     if (e != cudaSuccess) return e;
-    const uint64_t ewarps = (uint64_t)K * G.A;
-    const uint64_t eblocks = (ewarps * 32 + 255) / 256;
-    const uint64_t ecap = (uint64_t)sms * 8;
-    k_heavy_expand<<<(unsigned)(eblocks < ecap ? eblocks : ecap), 256, 0, s>>>(G, cube, W.heavy.list, W.heavy.ctr,
-                                                                             K, W.heavy.bits);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the residual's row-tile pass in the room after the residual regions
     const uint64_t rw = 2 * (uint64_t)R.nreg * R.rcap;
     BinWs W2 = W;

@@ -113,16 +113,23 @@ constexpr uint32_t kCountTile = 4 * kCountThreads;
 // already oriented, one segment of regions of rcap entries whose first
 // rcount[r] are valid (rcap a multiple of every tile and block size).
 // samp > 1: only every samp-th tile of kCountTile packets is counted (a
-// sample for run capacities, see sample_capacity).
+// sample for run capacities, see sample_capacity).  The first ncount blocks
+// count; a residual pass's blocks after them OR the heavy sources' bitmaps
+// into their columns (X).
 template <bool MULTI, bool ORIENT, bool RESID>
 __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const BinSegs S, uint64_t n, uint32_t nb,
                                                             uint32_t *__restrict__ counts, uint32_t samp,
-                                                            const uint32_t *__restrict__ rcount, uint64_t rcap) {
+                                                            const uint32_t *__restrict__ rcount, uint64_t rcap,
+                                                            uint32_t ncount, const HeavyExpand X) {
     extern __shared__ uint32_t hist[];
+    if (RESID && blockIdx.x >= ncount) {              // whole blocks: no barrier below is reached
+        heavy_expand_part(G, S.cube[0], X, blockIdx.x - ncount, gridDim.x - ncount);
+        return;
+    }
     uint64_t lo, hi, step;
     if (MULTI) {
         const uint64_t tiles = (n + kCountTile - 1) / kCountTile;
-        const uint64_t per = ((tiles + gridDim.x - 1) / gridDim.x + samp - 1) / samp * samp;
+        const uint64_t per = ((tiles + ncount - 1) / ncount + samp - 1) / samp * samp;
         lo = (uint64_t)blockIdx.x * per * kCountTile;
         hi = lo + per * kCountTile < n ? lo + per * kCountTile : n;
         if (lo > hi) lo = hi;                              // a block past the end counts nothing
@@ -130,7 +137,7 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
     } else {
         lo = (uint64_t)blockIdx.x * kCountTile * samp;
         hi = n;
-        step = (uint64_t)gridDim.x * kCountTile * samp;
+        step = (uint64_t)ncount * kCountTile * samp;
     }
     BlockTiles B;
     if (MULTI && lo < hi) {
@@ -768,7 +775,16 @@ static cudaError_t rowtile_pass(const Geo &G, const BinSegs &S, uint64_t m, uint
     // split a row tile only when it holds more than apply_ips/2 times the average tile
     uint64_t ch = (m * apply_ips / 2 + nb - 1) / nb;
     if (ch < (1u << 12)) ch = 1u << 12;
-    kcount<<<cgrid, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, span, nb, W.counts, samp, rcount, rcap);
+    // a residual pass: blocks for the heavy bitmaps' expansion after the counting blocks
+    const HeavyExpand X = RESID ? R->x : HeavyExpand{nullptr, nullptr, nullptr, 0};
+    uint32_t eblocks = 0;
+    if (X.list) {
+        const uint64_t ew = (uint64_t)X.kmax * G.A * 32;
+        const uint64_t eb = (ew + kCountThreads - 1) / kCountThreads, ecap = (uint64_t)sms * 8;
+        eblocks = (uint32_t)(eb < ecap ? eb : ecap);
+    }
+    kcount<<<cgrid + eblocks, kCountThreads, sizeof(uint32_t) * nb, s>>>(G, S, span, nb, W.counts, samp, rcount,
+                                                                          rcap, cgrid, X);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_bin_scan(W.counts, nb, (uint32_t)ch, W, s, samp)) != cudaSuccess) return e;
     Overflow O{nullptr, nullptr, 0};
