@@ -40,13 +40,13 @@ def update_kernels(partitioned: bool, tuning: dict, n: int) -> int:
     """Kernels of one single-cube update call of n packets (one pass of up to the workspace's
     packets): direct 1; partitioned count, scan, scatter, apply (with sampled run capacities the apply
     also drains the overflow list), and with the heavy-source split (on by default for row tiles and
-    passes of >= 4Mi packets) sample, histogram, select and split before them (the residual's counting
-    kernel also ORs the heavy bitmaps into their columns)."""
+    passes of >= 4Mi packets) sample, histogram and split (whose blocks pick the heavy sources) before
+    them (the residual's counting kernel also ORs the heavy bitmaps into their columns)."""
     if not partitioned:
         return 1
     heavy = tuning.get("heavy", 0)
     split = tuning.get("tile_kind", 0) != 1 and heavy != 1 and (heavy >= 2 or n >= 4 << 20)
-    return 8 if split else 4
+    return 7 if split else 4
 
 
 def detect_kernels(geo: dict) -> int:
@@ -627,8 +627,8 @@ def run_cbaa(args):
             "worst_ms": tuned["worst_ms"], "candidates": tuned["candidates"]},
         "tuning": C.get_tuning(),
         "roofline": {"bound": "hbm", "kernel": f"update ({path}: " +
-                     ({8: "heavy sample+hist+select+split, residual count (with the heavy bitmaps' "
-                         "expansion)+scan+scatter+apply",
+                     ({7: "heavy sample+hist+split (selection in each split block), residual count (with the "
+                         "heavy bitmaps' expansion)+scan+scatter+apply",
                        4: "count+scan+scatter+apply", 1: "k_update"}[
                          update_kernels(uws is not None, C.get_tuning(), pass_n)]) + ")",
                      "achieved": 8 * n / upd_s / 1e9, "peak": hbm_peak, "unit": "GB/s",

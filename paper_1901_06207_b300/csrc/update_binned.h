@@ -40,10 +40,10 @@ inline size_t bin_align(size_t x) { return (x + 255) / 256 * 256; }
 // so a heavy source's packets are gathered in one row bitmap of W words in
 // shared memory and ORed into its columns once.  Tables:
 //   a sample table of 2^15 slots (count, a key) indexed by the top 15 bits of
-//   the source key (a multiplicative bijection of the inner address), a
-//   lookup image of 2^14 entries (top 14 bits of the key -> its low 18 bits
-//   << 14 | heavy index), the heavy sources' keys, their row bitmaps, and
-//   counters.
+//   the source key (a multiplicative bijection of the inner address), the
+//   heavy sources' keys, their row bitmaps, and counters.  Each split block
+//   builds its own lookup image of 2^14 entries (top 14 bits of the key ->
+//   its low 18 bits << 14 | heavy index) in shared memory.
 constexpr uint32_t kHeavyCountBits = 15;
 constexpr uint32_t kHeavyTabBits = 14;
 constexpr uint32_t kHeavyTagBits = 32 - kHeavyTabBits;            // 18
@@ -64,7 +64,6 @@ constexpr uint32_t kHeavyRegionAlign = 16384;                      // region cap
 
 struct HeavyWs {
     uint32_t *count, *key;        // sample table [2^kHeavyCountBits]
-    uint32_t *tab;                // lookup image [2^kHeavyTabBits]
     uint32_t *list;               // key of heavy source h [kHeavyMax]
     uint32_t *bits;               // row bitmaps [kHeavyMax][W]
     uint32_t *ctr;                // counters [kHeavyCtrWords]
@@ -77,8 +76,7 @@ inline size_t heavy_clear_bytes(const Geo &G) {
 }
 
 inline size_t heavy_ws_bytes(const Geo &G) {
-    return 2 * bin_align(sizeof(uint32_t) << kHeavyCountBits) + bin_align(sizeof(uint32_t) << kHeavyTabBits) +
-           bin_align(sizeof(uint32_t) * kHeavyMax) + bin_align(sizeof(uint32_t) * (size_t)kHeavyMax * G.W) +
+    return 2 * bin_align(sizeof(uint32_t) << kHeavyCountBits) + bin_align(sizeof(uint32_t) * kHeavyMax) + bin_align(sizeof(uint32_t) * (size_t)kHeavyMax * G.W) +
            bin_align(sizeof(uint32_t) * kHeavyCtrWords);
 }
 
@@ -146,8 +144,6 @@ inline bool bin_ws_make(const Geo &G, uint32_t n_cubes, void *base, size_t bytes
     h += bin_align(sizeof(uint32_t) * kHeavyCtrWords);
     W->heavy.key = reinterpret_cast<uint32_t *>(h);
     h += bin_align(sizeof(uint32_t) << kHeavyCountBits);
-    W->heavy.tab = reinterpret_cast<uint32_t *>(h);
-    h += bin_align(sizeof(uint32_t) << kHeavyTabBits);
     W->heavy.list = reinterpret_cast<uint32_t *>(h);
     W->codes = reinterpret_cast<uint32_t *>(b + fixed);
     W->words = words;
@@ -175,7 +171,7 @@ __host__ __device__ __forceinline__ uint32_t heavy_key(uint32_t ip) { return ip 
 // counting kernel ORs into their columns (list null: nothing to expand).
 struct HeavyExpand {
     const uint32_t *list;          // key of heavy source h
-    const uint32_t *ctr;           // [0], [1]: sources taken (see k_heavy_select)
+    const uint32_t *ctr;           // [0], [1]: sources taken (see split_select)
     const uint32_t *bits;          // row bitmaps, W words per source
     uint32_t kmax;
 };

@@ -12,10 +12,11 @@
 //   1. k_heavy_sample : one tile of 1024 packets in 128 is counted by the top
 //                       15 bits of the source key (with a key seen in each
 //                       slot)
-//   2. k_heavy_hist, k_heavy_select : the most counted slots, up to K of
-//                       them, become the heavy sources; a lookup table maps a
-//                       key to its heavy index (top 14 bits -> low 18 bits as
-//                       a tag and the index)
+//   2. k_heavy_hist   : the sample counts' histogram; from it every split
+//                       block picks the most counted slots, up to K of them,
+//                       as the heavy sources (the same ones in every block)
+//                       and builds a lookup table from key to heavy index
+//                       (top 14 bits -> low 18 bits as a tag and the index)
 //   3. k_heavy_split  : every packet: a heavy source's row bit is set in
 //                       its bitmap in shared memory (a bit already set is
 //                       only read); any other packet is written out as
@@ -125,38 +126,51 @@ __device__ __forceinline__ uint32_t count_bin(uint32_t c) {
 __device__ __forceinline__ uint32_t bin_floor(uint32_t b) { return (4u + (b & 3u)) << ((b >> 2) - 2); }
 
 // Histogram of the sample counts by quarter octave (one slot per thread).
-// Also readies what the pass uses next: the lookup table empty (kTabWords
-// entries spread over the blocks) and the row-tile counts zero (nzero words).
+// Also zeroes the residual pass's row-tile counts (nzero words).
 __global__ void __launch_bounds__(1024) k_heavy_hist(const uint32_t *__restrict__ count, uint32_t *__restrict__ hist,
-                                                     uint32_t *__restrict__ tab, uint32_t *__restrict__ zero,
-                                                     uint32_t nzero) {
+                                                     uint32_t *__restrict__ zero, uint32_t nzero) {
     __shared__ uint32_t h[kHeavyHistBins];
     if (threadIdx.x < kHeavyHistBins) h[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t b = i < kCountSlots ? count_bin(__ldcg(count + i)) : kHeavyHistBins;
     if (b < kHeavyHistBins) atomicAdd(&h[b], 1u);
-    for (uint32_t t = i; t < kTabWords; t += gridDim.x * blockDim.x) tab[t] = kHeavyEmpty;
     for (uint32_t t = i; t < nzero; t += gridDim.x * blockDim.x) zero[t] = 0u;
     __syncthreads();
     if (threadIdx.x < kHeavyHistBins && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
 }
 
-// Heavy sources (one slot per thread): every slot counted at least thr
-// times, thr the smallest bin floor that selects at most kmax slots, then
-// slots of the bin below thr while room is left.  Upper slots take indices
-// [0, acc) from ctr[0], the others acc + ctr[1] (dropped from kmax on).  Two
-// sources whose lookup entries collide: the one that loses the CAS stays on
-// the row-tile path.  tab starts all empty.
-__global__ void __launch_bounds__(1024) k_heavy_select(const uint32_t *__restrict__ count,
-                                                       const uint32_t *__restrict__ key, uint32_t kmax,
-                                                       uint32_t *__restrict__ tab, uint32_t *__restrict__ list,
-                                                       uint32_t *__restrict__ ctr) {
-    __shared__ uint32_t s_thr, s_lo, s_acc;
-    __shared__ uint32_t hist[kHeavyHistBins];
-    if (threadIdx.x < kHeavyHistBins) hist[threadIdx.x] = __ldcg(ctr + kHeavyCtrHist + threadIdx.x);
+// The heavy sources, chosen again by every split block from the sample
+// (1024 threads, 32 slots each kept in registers), so that no launch of its
+// own stands between the histogram and the split: thr is the smallest bin
+// floor whose bins and the ones above hold at most kmax slots; every slot
+// counted at least thr times (and kHeavyMinCount) takes an index in
+// [0, acc), in slot order, then slots of the bin below thr take acc, acc + 1,
+// ... while room is left.  The indices come from block-wide prefix sums in
+// slot order, so every block assigns the same index to the same source, and
+// block 0 lists the keys for the expansion (ctr[0], ctr[1]: the upper and
+// lower slots taken).  Each block enters the keys into its own lookup image
+// in shared memory; two keys whose entries collide: the one that loses the
+// CAS stays on the row-tile path in that block (which sources are heavy
+// only decides the path of a packet).  Also clears the bitmaps.
+template <uint32_t THREADS>
+__device__ __forceinline__ void split_select(const uint32_t *__restrict__ count, const uint32_t *__restrict__ key,
+                                             const uint32_t *__restrict__ hist_g, uint32_t kmax, uint32_t *tab,
+                                             uint32_t *bm, uint32_t kwords, uint32_t *__restrict__ list_g,
+                                             uint32_t *__restrict__ ctr_g) {
+    static_assert(THREADS * 32 == kCountSlots, "32 sample slots per thread");
+    __shared__ uint32_t hist[kHeavyHistBins], s_thr, s_lo, s_acc, s_wu[32], s_wl[32];
+    const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+    uint32_t c[32];
+#pragma unroll
+    for (uint32_t j = 0; j < 32; ++j) c[j] = __ldcg(count + t + THREADS * j);
+    if (t < kHeavyHistBins) hist[t] = __ldcg(hist_g + t);
+    uint4 *t4 = reinterpret_cast<uint4 *>(tab);
+    for (uint32_t i = t; i < kTabWords / 4; i += THREADS) t4[i] = make_uint4(kHeavyEmpty, kHeavyEmpty, kHeavyEmpty, kHeavyEmpty);
+    uint4 *b4 = reinterpret_cast<uint4 *>(bm);
+    for (uint32_t i = t; i < kwords / 4; i += THREADS) b4[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
-    if (threadIdx.x == 0) {                            // from shared memory: no global round trip per bin
+    if (t == 0) {                                     // from shared memory: no global round trip per bin
         uint32_t acc = 0, thr = 0xFFFFFFFFu, lo = 0xFFFFFFFFu;
         for (int b = (int)kHeavyHistBins - 1; b >= 0; --b) {
             const uint32_t hb = hist[b];
@@ -172,24 +186,62 @@ __global__ void __launch_bounds__(1024) k_heavy_select(const uint32_t *__restric
         s_acc = acc;
     }
     __syncthreads();
-    const uint32_t thr = s_thr, lo = s_lo, acc = s_acc, lane = threadIdx.x & 31u;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t c = i < kCountSlots ? __ldcg(count + i) : 0u;
-    const bool up = c >= thr && c >= kHeavyMinCount, low = !up && c >= lo && c >= kHeavyMinCount;
-    // one reservation per warp for each kind
-    const uint32_t wu = __ballot_sync(0xffffffffu, up), wl = __ballot_sync(0xffffffffu, low);
-    uint32_t fu = 0, fl = 0;
-    if (wu && lane == __ffs(wu) - 1) fu = atomicAdd(ctr + 0, __popc(wu));
-    if (wl && lane == __ffs(wl) - 1) fl = atomicAdd(ctr + 1, __popc(wl));
-    fu = wu ? __shfl_sync(0xffffffffu, fu, __ffs(wu) - 1) : 0u;
-    fl = wl ? __shfl_sync(0xffffffffu, fl, __ffs(wl) - 1) : 0u;
-    if (!up && !low) return;
-    const uint32_t below = (1u << lane) - 1u;
-    const uint32_t h = up ? fu + __popc(wu & below) : acc + fl + __popc(wl & below);
-    if (h >= kmax) return;                              // the partial bin only while room is left
-    const uint32_t k = __ldcg(key + i);
-    list[h] = k;
-    atomicCAS(&tab[k >> kHeavyTagBits], kHeavyEmpty, ((k & kTagMask) << kHeavyTabBits) | h);
+    const uint32_t thr = s_thr, lo = s_lo, acc = s_acc;
+    uint32_t mu = 0, ml = 0;                          // bit j: slot t + THREADS j taken (upper / lower)
+#pragma unroll
+    for (uint32_t j = 0; j < 32; ++j) {
+        const bool up = c[j] >= thr && c[j] >= kHeavyMinCount;
+        const bool low = !up && c[j] >= lo && c[j] >= kHeavyMinCount;
+        mu |= (uint32_t)up << j;
+        ml |= (uint32_t)low << j;
+    }
+    // indices in (thread, j) order: an exclusive prefix of the threads' counts
+    const uint32_t nu = __popc(mu), nl = __popc(ml);
+    uint32_t xu = nu, xl = nl;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t yu = __shfl_up_sync(0xffffffffu, xu, o), yl = __shfl_up_sync(0xffffffffu, xl, o);
+        if (lane >= o) {
+            xu += yu;
+            xl += yl;
+        }
+    }
+    if (lane == 31) {
+        s_wu[warp] = xu;
+        s_wl[warp] = xl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t vu = s_wu[lane], vl = s_wl[lane];
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t yu = __shfl_up_sync(0xffffffffu, vu, o), yl = __shfl_up_sync(0xffffffffu, vl, o);
+            if (lane >= o) {
+                vu += yu;
+                vl += yl;
+            }
+        }
+        s_wu[lane] = vu;                               // inclusive over warps
+        s_wl[lane] = vl;
+    }
+    __syncthreads();
+    uint32_t hu = (warp ? s_wu[warp - 1] : 0u) + xu - nu;
+    uint32_t hl = acc + (warp ? s_wl[warp - 1] : 0u) + xl - nl;
+    if (blockIdx.x == 0 && t == 0) {
+        ctr_g[0] = s_wu[31];
+        ctr_g[1] = s_wl[31];
+    }
+    uint32_t sel = mu | ml;
+    while (sel) {
+        const uint32_t j = __ffs(sel) - 1u;
+        sel &= sel - 1u;
+        const uint32_t h = ((mu >> j) & 1u) ? hu++ : hl++;
+        if (h >= kmax) continue;                       // the partial bin only while room is left
+        const uint32_t k = __ldcg(key + t + THREADS * j);
+        if (blockIdx.x == 0) list_g[h] = k;
+        atomicCAS(&tab[k >> kHeavyTagBits], kHeavyEmpty, ((k & kTagMask) << kHeavyTabBits) | h);
+    }
+    __syncthreads();
 }
 
 // Packets of chunk c (32 lanes x 8 packets, 2 per 16-byte load) into q;
@@ -321,28 +373,21 @@ __device__ __forceinline__ void split_flush(const uint32_t *bm, uint32_t kwords,
     }
 }
 
-// Loads the lookup table and clears the bitmaps in shared memory.
-template <uint32_t THREADS>
-__device__ __forceinline__ void split_prologue(const uint32_t *tab_g, uint32_t *tab, uint32_t *bm, uint32_t kwords) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(tab_g);
-    uint4 *dst = reinterpret_cast<uint4 *>(tab);
-    for (uint32_t i = threadIdx.x; i < kTabWords / 4; i += THREADS) dst[i] = __ldg(src + i);
-    uint4 *b4 = reinterpret_cast<uint4 *>(bm);
-    for (uint32_t i = threadIdx.x; i < kwords / 4; i += THREADS) b4[i] = make_uint4(0u, 0u, 0u, 0u);
-}
-
 // Every warp walks its own chunks of 256 packets (chunk c for c = global
 // warp, + all warps, ...), the next chunk's 16-byte loads in flight in
 // registers while it works on the current one (two register sets used in
 // turn, so nothing is copied between them).  Shared memory: the lookup
-// table, then K row bitmaps of W words (kwords words).  Residual entries go
+// table (built by split_select), then K row bitmaps of W words (kwords
+// words).  Residual entries go
 // to this block's region (rcap entries from blockIdx.x * rcap), one
 // shared-memory reservation per warp and chunk; the region's count is
 // written at the end.
 template <uint32_t THREADS, uint32_t MINB, bool ORIENT>
 __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, const uint32_t *__restrict__ pairs,
-                                                               uint64_t n, const uint32_t *__restrict__ tab_g,
+                                                               uint64_t n, const uint32_t *__restrict__ count,
+                                                               const uint32_t *__restrict__ key, uint32_t kmax,
                                                                uint32_t kwords, uint32_t *__restrict__ bits_g,
+                                                               uint32_t *__restrict__ list, uint32_t *__restrict__ ctr,
                                                                uint2 *__restrict__ resid, uint64_t rcap,
                                                                uint32_t *__restrict__ rcount) {
     extern __shared__ __align__(16) uint32_t sm[];
@@ -350,8 +395,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
     uint32_t *bm = sm + kTabWords;
     __shared__ uint32_t s_cnt;
     const uint32_t tid = threadIdx.x, lane = tid & 31u;
-    split_prologue<THREADS>(tab_g, tab, bm, kwords);
     if (tid == 0) s_cnt = 0;
+    split_select<THREADS>(count, key, ctr + kHeavyCtrHist, kmax, tab, bm, kwords, list, ctr);
     __syncthreads();
     uint2 *region = resid + (uint64_t)blockIdx.x * rcap;
     const uint32_t bm_s = static_cast<uint32_t>(__cvta_generic_to_shared(bm));
@@ -415,14 +460,14 @@ Residual residual_layout(const cbaa_tuning &T, uint64_t m, const uint32_t *entri
 }
 
 template <uint32_t THREADS, uint32_t MINB, bool ORIENT>
-cudaError_t launch_split(const Geo &G, const uint32_t *pairs, uint64_t m, const BinWs &W, uint32_t kwords,
-                         const Residual &R, cudaStream_t s) {
+cudaError_t launch_split(const Geo &G, const uint32_t *pairs, uint64_t m, const BinWs &W, uint32_t K,
+                         uint32_t kwords, const Residual &R, cudaStream_t s) {
     auto k = k_heavy_split<THREADS, MINB, ORIENT>;
     const size_t smem = sizeof(uint32_t) * ((size_t)kTabWords + kwords);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
-    k<<<R.nreg, THREADS, smem, s>>>(G, pairs, m, W.heavy.tab, kwords, W.heavy.bits,
-                                    const_cast<uint2 *>(R.entries), R.rcap, W.heavy.rcount());
+    k<<<R.nreg, THREADS, smem, s>>>(G, pairs, m, W.heavy.count, W.heavy.key, K, kwords, W.heavy.bits, W.heavy.list,
+                                    W.heavy.ctr, const_cast<uint2 *>(R.entries), R.rcap, W.heavy.rcount());
     return cudaGetLastError();
 }
 
@@ -441,15 +486,11 @@ cudaError_t heavy_pass(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint
         G, pairs, m, W.heavy.count, W.heavy.key);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const uint32_t nb = rowtile_bins(G, 1);
-    k_heavy_hist<<<kCountSlots / 1024, 1024, 0, s>>>(W.heavy.count, W.heavy.ctr + kHeavyCtrHist, W.heavy.tab,
-                                                     W.counts, nb + 1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_heavy_select<<<kCountSlots / 1024, 1024, 0, s>>>(W.heavy.count, W.heavy.key, K, W.heavy.tab, W.heavy.list,
-                                                      W.heavy.ctr);
+    k_heavy_hist<<<kCountSlots / 1024, 1024, 0, s>>>(W.heavy.count, W.heavy.ctr + kHeavyCtrHist, W.counts, nb + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     Residual R = residual_layout(T, m, W.codes, W.heavy.rcount());
     R.x = HeavyExpand{W.heavy.list, W.heavy.ctr, W.heavy.bits, K};
-    e = launch_split<1024, 1, ORIENT>(G, pairs, m, W, kwords, R, s);
+    e = launch_split<1024, 1, ORIENT>(G, pairs, m, W, K, kwords, R, s);
     if (e != cudaSuccess) return e;
     // the residual's row-tile pass in the room after the residual regions
     const uint64_t rw = 2 * (uint64_t)R.nreg * R.rcap;
