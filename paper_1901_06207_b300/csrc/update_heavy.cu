@@ -9,7 +9,7 @@
 // core-network traffic a few sources carry most packets (super hosts and
 // the head of a Zipf law), so:
 //
-//   1. k_heavy_sample : one tile of 1024 packets in 128 is counted by the top
+//   1. k_heavy_sample : one tile of 1024 packets in 256 is counted by the top
 //                       15 bits of the source key (with a key seen in each
 //                       slot)
 //   2. k_heavy_hist   : the sample counts' histogram; from it every split
@@ -44,7 +44,7 @@ namespace {
 
 constexpr uint32_t kSampleThreads = 1024;
 constexpr uint32_t kSampleTile = 1024;                 // packets of a sample tile, one per thread
-constexpr uint32_t kHeavySampleEvery = 128;            // one sample tile in 128
+constexpr uint32_t kHeavySampleEvery = 256;            // one sample tile in 256
 constexpr uint32_t kHeavyMinCount = 4;                 // sampled packets a heavy source needs at least
 constexpr uint64_t kHeavyMinPackets = 4ull << 20;      // default: passes of at least this many packets
 constexpr uint32_t kTabWords = 1u << kHeavyTabBits;
@@ -482,7 +482,9 @@ cudaError_t heavy_pass(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint
     const size_t count_smem = sizeof(uint32_t) * kCountSlots;
     if ((e = allow_smem(k_heavy_sample<ORIENT>, count_smem)) != cudaSuccess) return e;
     const uint64_t tiles = (m + (uint64_t)kSampleTile * kHeavySampleEvery - 1) / ((uint64_t)kSampleTile * kHeavySampleEvery);
-    k_heavy_sample<ORIENT><<<(unsigned)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms), kSampleThreads, count_smem, s>>>(
+    // half the SMs: every block scans and flushes its whole 2^15-slot table, so fewer, fuller blocks
+    const uint64_t sblocks = (uint64_t)(sms > 1 ? sms / 2 : 1);
+    k_heavy_sample<ORIENT><<<(unsigned)(tiles < sblocks ? tiles : sblocks), kSampleThreads, count_smem, s>>>(
         G, pairs, m, W.heavy.count, W.heavy.key);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const uint32_t nb = rowtile_bins(G, 1);
