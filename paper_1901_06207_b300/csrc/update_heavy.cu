@@ -299,11 +299,15 @@ __device__ __forceinline__ void st_pair_if(uint2 *ptr, uint32_t x, uint32_t y, u
 // branches: the sets and the stores are predicated.  bm_s: the shared
 // address of bm; kmask: heavy sources in bm - 1 (a power of two less one);
 // seed_fold: the row hash's seed folded for row_of_folded.
-template <uint32_t NP, bool ORIENT>
+// FULL (every lane holds all NP packets, no inner network): the presence
+// bits are known to be set and are not tested.
+template <uint32_t NP, bool ORIENT, bool FULL>
 __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab, const uint32_t *bm, uint32_t bm_s,
                                               uint32_t kmask, uint32_t seed_fold, uint32_t (&a)[NP],
                                               uint32_t (&b)[NP], uint32_t ok, uint2 *region, uint32_t *s_cnt,
                                               uint32_t lane) {
+    static_assert(!(FULL && ORIENT), "orientation may drop packets");
+    if (FULL) ok = (1u << NP) - 1u;
     uint32_t row[NP], e[NP];
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
@@ -318,7 +322,7 @@ __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab,
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
         const uint32_t d = e[k] ^ (a[k] * (kHeavyKeyMul << kHeavyTabBits));
-        const bool hv = ((ok >> k) & 1u) && d < kHeavyIdxMask;
+        const bool hv = (FULL || ((ok >> k) & 1u)) && d < kHeavyIdxMask;
         heavy |= (uint32_t)hv << k;
         // the bitmap word; for a packet that is not heavy some source's word (d & kmask
         // < K), read and never set
@@ -342,12 +346,12 @@ __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab,
     uint32_t base = 0;
     if (lane == 31 && x) base = atomicAdd(s_cnt, x);
     base = __shfl_sync(0xffffffffu, base, 31) + x - cnt;
-    uint2 *out = region + base;                                // this lane's entries, in slot order
+    uint32_t at = base;                                        // this lane's entries, in slot order
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
         const uint32_t kk = (keep >> k) & 1u;
-        st_pair_if(out, a[k], row[k], kk);
-        out += kk;
+        st_pair_if(region + at, a[k], row[k], kk);
+        at += kk;
     }
 }
 
@@ -417,7 +421,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
             a[k] = (k & 1u) ? q[k / 2].z : q[k / 2].x;
             b[k] = (k & 1u) ? q[k / 2].w : q[k / 2].y;
         }
-        split_packets<8, ORIENT>(G, tab, bm, bm_s, kmask, seed_fold, a, b, ok, region, &s_cnt, lane);
+        if (!ORIENT && __all_sync(0xffffffffu, ok == 0xFFu))      // the same path for the whole warp
+            split_packets<8, false, true>(G, tab, bm, bm_s, kmask, seed_fold, a, b, ok, region, &s_cnt, lane);
+        else
+            split_packets<8, ORIENT, false>(G, tab, bm, bm_s, kmask, seed_fold, a, b, ok, region, &s_cnt, lane);
 #pragma unroll
         for (uint32_t j = 0; j < 4; ++j) q[j] = qn[j];
         ok = okn;
