@@ -277,11 +277,10 @@ __device__ __forceinline__ uint32_t split_load(const uint32_t *pairs, uint64_t n
     return ok;
 }
 
-// Shared-memory OR of `bit` into the word at shared address `sa` when `p`;
-// predicated, so that no branch surrounds it.
-__device__ __forceinline__ void red_or_shared_if(uint32_t sa, uint32_t bit, uint32_t p) {
-    asm volatile("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q red.shared.or.b32 [%0], %1; }"
-                 :: "r"(sa), "r"(bit), "r"(p) : "memory");
+// Shared-memory OR of v into the word at shared address sa, issued by every
+// lane (v = 0 where nothing is to be set: no predicate, no branch).
+__device__ __forceinline__ void red_or_shared(uint32_t sa, uint32_t v) {
+    asm volatile("red.shared.or.b32 [%0], %1;" :: "r"(sa), "r"(v) : "memory");
 }
 
 // 8-byte store of {x, y} to `ptr` when `p` (predicated).
@@ -296,7 +295,8 @@ __device__ __forceinline__ void st_pair_if(uint2 *ptr, uint32_t x, uint32_t y, u
 // still clear; the others' entries {iip, row} (oriented) written to `region`
 // at places reserved with one shared-memory atomic per warp.  In phases, so
 // that the lanes' shared-memory reads are in flight together, and without
-// branches: the sets and the stores are predicated.  bm_s: the shared
+// branches: every lane ORs (0 where nothing is to be set), the stores are
+// predicated.  bm_s: the shared
 // address of bm; kmask: heavy sources in bm - 1 (a power of two less one);
 // seed_fold: the row hash's seed folded for row_of_folded.
 // FULL (every lane holds all NP packets, no inner network): the presence
@@ -333,7 +333,7 @@ __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab,
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
         const uint32_t bit = __funnelshift_l(0u, 1u, row[k]);      // 1 << (row & 31)
-        red_or_shared_if(bm_s + 4u * wi[k], bit, ((heavy >> k) & 1u) & (uint32_t)!(wv[k] & bit));
+        red_or_shared(bm_s + 4u * wi[k], (((heavy >> k) & 1u) && !(wv[k] & bit)) ? bit : 0u);
     }
     const uint32_t keep = ok & ~heavy;
     const uint32_t cnt = __popc(keep);
