@@ -532,66 +532,92 @@ __global__ void __launch_bounds__(kApplyThreads, 1) k_rt_apply_pair(const Geo G,
     const uint32_t quads = tile_words / 4;                 // arrays start at multiples of 32 words
     for (uint32_t q = threadIdx.x; q < 2 * quads; q += blockDim.x)
         reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
-    for (;;) {
+    // An item's records as one stream: tile 2k's run, then tile 2k + 1's (records written: up to
+    // the run's end, or fewer when its capacity came from a sample).  Items are fetched one
+    // ahead, so that the next item's first records load while the current one is flushed.
+    struct Stream {
+        uint32_t a0, len_a, b0, len;
+    };
+    auto stream_of = [&](uint32_t kk) {
+        Stream st{0u, 0u, 0u, 0u};
+        if (kk < npairs) {
+            const uint32_t b = 2 * kk;
+            const uint32_t a1 = offsets[b + 1] < cursors[b] ? offsets[b + 1] : cursors[b];
+            const uint32_t b1 = offsets[b + 2] < cursors[b + 1] ? offsets[b + 2] : cursors[b + 1];
+            st.a0 = offsets[b];
+            st.len_a = a1 > st.a0 ? a1 - st.a0 : 0u;
+            st.b0 = offsets[b + 1];
+            st.len = st.len_a + (b1 > st.b0 ? b1 - st.b0 : 0u);
+        }
+        return st;
+    };
+    auto rec_at = [&](const Stream &st, uint32_t q) {
+        return recs + (q < st.len_a ? st.a0 + q : st.b0 + (q - st.len_a));
+    };
+    constexpr uint32_t U = 8;                          // records in flight per thread (and the next U)
+    const uint32_t T = blockDim.x;
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+    __syncthreads();
+    uint32_t k = s_item;
+    Stream st = stream_of(k);
+    uint32_t pos = threadIdx.x;
+    Rec rv[U];
+    bool full = pos + (U - 1) * T < st.len;
+    if (full) {
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) rv[u] = __ldcs(rec_at(st, pos + u * T));
+    }
+    while (k < npairs) {
+        __syncthreads();                              // the previous flush's zeros are written; s_item read
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
-        __syncthreads();
-        const uint32_t k = s_item;
-        if (k >= npairs) break;
-        bool any = false;
+        while (full) {
+            const uint32_t pn = pos + U * T;
+            const bool next = pn + (U - 1) * T < st.len;
+            Rec rn[U];
+            if (next) {
 #pragma unroll
-        for (uint32_t h = 0; h < 2; ++h) {
-            const uint32_t b = 2 * k + h;
-            // records written: up to the run's end, or fewer when its capacity came from a sample
-            const uint32_t c0 = offsets[b];
-            const uint32_t c1 = offsets[b + 1] < cursors[b] ? offsets[b + 1] : cursors[b];
-            any |= c1 > c0;
-            uint32_t *tl = h ? t1 : tile;
-            uint32_t c = c0 + threadIdx.x;
-            // eight records in flight, the next eight loaded while these are set (one block per
-            // SM leaves registers for it)
-            constexpr uint32_t U = 8;
-            Rec rv[U];
-            bool full = c + (U - 1) * blockDim.x < c1;
-            if (full) {
-#pragma unroll
-                for (uint32_t u = 0; u < U; ++u) rv[u] = __ldcs(recs + c + u * blockDim.x);
+                for (uint32_t u = 0; u < U; ++u) rn[u] = __ldcs(rec_at(st, pn + u * T));
             }
-            while (full) {
-                const uint32_t cn = c + U * blockDim.x;
-                const bool next = cn + (U - 1) * blockDim.x < c1;
-                Rec rn[U];
-                if (next) {
 #pragma unroll
-                    for (uint32_t u = 0; u < U; ++u) rn[u] = __ldcs(recs + cn + u * blockDim.x);
-                }
+            for (uint32_t u = 0; u < U; ++u)
+                rt_apply_rec<NRA, NVA, false>(G, pos + u * T < st.len_a ? tile : t1, rv[u]);
 #pragma unroll
-                for (uint32_t u = 0; u < U; ++u) rt_apply_rec<NRA, NVA, false>(G, tl, rv[u]);
+            for (uint32_t u = 0; u < U; ++u) rv[u] = rn[u];
+            pos = pn;
+            full = next;
+        }
+        for (; pos < st.len; pos += T)
+            rt_apply_rec<NRA, NVA, false>(G, pos < st.len_a ? tile : t1, __ldcs(rec_at(st, pos)));
+        __syncthreads();                              // the item's tiles are complete
+        const uint32_t kn = s_item;
+        const Stream sn = stream_of(kn);
+        // the next item's first records, in flight during the flush
+        pos = threadIdx.x;
+        full = pos + (U - 1) * T < sn.len;
+        if (full) {
 #pragma unroll
-                for (uint32_t u = 0; u < U; ++u) rv[u] = rn[u];
-                c = cn;
-                full = next;
+            for (uint32_t u = 0; u < U; ++u) rv[u] = __ldcs(rec_at(sn, pos + u * T));
+        }
+        if (st.len) {                                 // the same for every thread
+            const uint32_t cs = (2 * k) / G.W, w = 2 * k - cs * G.W;
+            uint32_t *cube = S.cube[0] + (size_t)cs * G.cs_words + w;
+            for (uint32_t q = threadIdx.x; q < quads; q += blockDim.x) {
+                const uint4 va = a4[q], vb = b4[q];
+                if (!(va.x | va.y | va.z | va.w | vb.x | vb.y | vb.z | vb.w)) continue;
+                const uint32_t t = 4 * q;
+                uint32_t a = 0;                               // array of tile words t .. t+3
+                while (a + 1 < G.A && t >= G.col_base[a + 1]) ++a;
+                uint32_t *dst = cube + G.arr_base[a] + (size_t)(t - G.col_base[a]) * G.W;
+                const uint32_t lo[4] = {va.x, va.y, va.z, va.w}, hi[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (lo[j] | hi[j]) red_or64(dst + j * G.W, ((uint64_t)hi[j] << 32) | lo[j]);
+                reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
+                reinterpret_cast<uint4 *>(t1)[q] = make_uint4(0u, 0u, 0u, 0u);
             }
-            for (; c < c1; c += blockDim.x) rt_apply_rec<NRA, NVA, false>(G, tl, __ldcs(recs + c));
         }
-        __syncthreads();
-        if (!any) continue;                               // the same for every thread
-        const uint32_t cs = (2 * k) / G.W, w = 2 * k - cs * G.W;
-        uint32_t *cube = S.cube[0] + (size_t)cs * G.cs_words + w;
-        for (uint32_t q = threadIdx.x; q < quads; q += blockDim.x) {
-            const uint4 va = a4[q], vb = b4[q];
-            if (!(va.x | va.y | va.z | va.w | vb.x | vb.y | vb.z | vb.w)) continue;
-            const uint32_t t = 4 * q;
-            uint32_t a = 0;                                   // array of tile words t .. t+3
-            while (a + 1 < G.A && t >= G.col_base[a + 1]) ++a;
-            uint32_t *dst = cube + G.arr_base[a] + (size_t)(t - G.col_base[a]) * G.W;
-            const uint32_t lo[4] = {va.x, va.y, va.z, va.w}, hi[4] = {vb.x, vb.y, vb.z, vb.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (lo[j] | hi[j]) red_or64(dst + j * G.W, ((uint64_t)hi[j] << 32) | lo[j]);
-            reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
-            reinterpret_cast<uint4 *>(t1)[q] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        __syncthreads();
+        k = kn;
+        st = sn;
     }
     // a sampled pass: blocks leaving the item queue take chunks of the overflow list
     if (!ovf) return;
