@@ -375,45 +375,47 @@ def run_cbaa(args):
     kernels_per_step = -(-n // pass_n) * update_kernels(uws is not None, C.get_tuning(), pass_n) + \
         detect_kernels(geo)
 
-    def do_update(c=None, src=None):
+    def do_update(c=None, src=None, u=None):
         c = cube if c is None else c
         src = pairs_dev if src is None else src
-        if uws is not None:
-            c.update_binned(src, uws)
+        u = uws if u is None else u
+        if u is not None:
+            c.update_binned(src, u)
         else:
             c.update(src)
 
-    # Double-buffered windows, as a deployed detector runs them: window k+1's
-    # reset and update (stream s_up, cube k+1 mod 2) overlap window k's detect
-    # (stream s_det, cube k mod 2); a cube is reset only after its previous
-    # detect finished.  Every window is fully updated and detected.
-    cubes2 = [cube, C.Cube(geo, device=dev)]
-    ws2 = [ws, C.Workspace(geo, max_candidates=1 << 18, device=dev)]
-    out2 = [out, torch.zeros(4 * cap, dtype=torch.int32, device=dev)]
-    info2 = [info, torch.zeros(8, dtype=torch.int32, device=dev)]
-    s_up, s_det = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    det_done = [None, None]
+    # Windows in flight on `lanes` lanes, as a deployed detector runs them when
+    # windows close faster than one window's update and detect take: lane j
+    # owns a stream, a cube, an update workspace, a detect workspace, its
+    # outputs and its own resident packet buffer; window k runs on lane
+    # k mod L as update, detect, reset in stream order, so that different
+    # windows' kernels overlap (one window's heavy split beside another's
+    # residual kernels and a third's detect).  Every window is fully updated
+    # and detected.
+    L = max(2, args.lanes)
+    lane_cube = [cube] + [C.Cube(geo, device=dev) for _ in range(L - 1)]
+    lane_uws = [uws] + [C.UpdateWorkspace(geo, args.workspace_packets or n, device=dev) if uws is not None else None
+                        for _ in range(L - 1)]
+    lane_ws = [ws] + [C.Workspace(geo, max_candidates=1 << 18, device=dev) for _ in range(L - 1)]
+    lane_out = [out] + [torch.zeros(4 * cap, dtype=torch.int32, device=dev) for _ in range(L - 1)]
+    lane_info = [info] + [torch.zeros(8, dtype=torch.int32, device=dev) for _ in range(L - 1)]
+    lane_pairs = [pairs_dev] + [pairs_dev.clone() for _ in range(L - 1)]
+    lane_stream = [torch.cuda.Stream(dev) for _ in range(L)]
+    lane_fresh = [True] * L
 
     def piped_step(k):
-        b = k & 1
-        with torch.cuda.stream(s_up):
-            if det_done[b] is None:
-                cubes2[b].reset()
-            else:
-                s_up.wait_event(det_done[b])      # detected and already reset on s_det
-            do_update(cubes2[b])
-            up = torch.cuda.Event()
-            up.record(s_up)
-        with torch.cuda.stream(s_det):
-            s_det.wait_event(up)
-            cubes2[b].detect_async(theta, ws2[b], out2[b], info2[b])
-            cubes2[b].reset()                     # the next window on this cube starts empty
-            det_done[b] = torch.cuda.Event()
-            det_done[b].record(s_det)
+        b = k % L
+        with torch.cuda.stream(lane_stream[b]):
+            if lane_fresh[b]:
+                lane_cube[b].reset()
+                lane_fresh[b] = False
+            do_update(lane_cube[b], lane_pairs[b], lane_uws[b])
+            lane_cube[b].detect_async(theta, lane_ws[b], lane_out[b], lane_info[b])
+            lane_cube[b].reset()                  # the lane's next window starts empty
 
     def join_streams():
-        stream.wait_stream(s_up)
-        stream.wait_stream(s_det)
+        for su in lane_stream:
+            stream.wait_stream(su)
 
     def step(ev=None):
         cube.reset()
@@ -433,7 +435,7 @@ def run_cbaa(args):
     assert inf["status"] == C.OK, inf
     if args.detect_only:
         pairs_dev = pairs_pin = uws = None            # the packets and the second buffers freed
-        cubes2[1] = ws2[1] = out2[1] = info2[1] = None
+        lane_cube = lane_ws = lane_out = lane_info = lane_pairs = lane_uws = None
         return detect_only(args, C, cube, ws, out, info, theta, stream, hosts)
 
     # L2 RED.OR roof on a buffer the size of the cube (the update kernel's bound)
@@ -518,8 +520,8 @@ def run_cbaa(args):
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         t_start.record(stream)
-        s_up.wait_stream(stream)
-        s_det.wait_stream(stream)
+        for su in lane_stream:
+            su.wait_stream(stream)
         for k in range(args.steps):
             piped_step(k)
         join_streams()
@@ -528,8 +530,8 @@ def run_cbaa(args):
     barrier(world)
     total_ms = t_start.elapsed_time(t_end)
     total_ms_max = reduce_over_ranks(total_ms, world, "max", dev)
-    for b in range(2):
-        h2, inf2 = C.hosts_from_device(out2[b], info2[b])
+    for b in range(L):
+        h2, inf2 = C.hosts_from_device(lane_out[b], lane_info[b])
         assert inf2["status"] == C.OK and inf2["n_hosts"] == inf["n_hosts"], (inf2, inf)
     packets_all = reduce_over_ranks(float(n), world, "sum", dev)
     value = packets_all * args.steps / (total_ms_max * 1e-3) / 1e9
@@ -537,13 +539,14 @@ def run_cbaa(args):
     # end to end through the public API with host buffers, windows pipelined
     # on three streams: H2D of window k+1's packets from pinned memory (s_copy)
     # overlaps window k's update (s_up) and detect + D2H of its host list and
-    # info into pinned host memory (s_det).  Two device packet buffers.
+    # info into pinned host memory (s_det).  Two device packet buffers, two
+    # cubes (lanes 0 and 1's).
     e2e_steps = max(3, min(args.steps, 10))
-    bufs = [pairs_dev, torch.empty_like(pairs_dev)]
+    bufs, cubes2, ws2, out2, info2 = lane_pairs[:2], lane_cube[:2], lane_ws[:2], lane_out[:2], lane_info[:2]
     host_out = [torch.empty(4 * cap, dtype=torch.int32).pin_memory() for _ in range(2)]
     host_info = [torch.empty(8, dtype=torch.int32).pin_memory() for _ in range(2)]
-    s_copy = torch.cuda.Stream(dev)
-    buf_free, det_done[0], det_done[1] = [None, None], None, None
+    s_copy, s_up, s_det = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    buf_free, det_done = [None, None], [None, None]
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -600,10 +603,12 @@ def run_cbaa(args):
         "metric": METRIC, "value": value, "unit": "Gpps", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {**desc, "l2": "inputs larger than L2: each step streams a 512 MiB packet buffer; "
-                                 "the 64 MiB cubes are L2-resident by design and re-zeroed every step",
-                   "pipelining": "double-buffered windows: a window's update (stream 1, cube k mod 2) overlaps "
-                                 "the previous window's detect and the reset that follows it (stream 2)",
+        "config": {**desc, "l2": "inputs larger than L2: each step streams a 512 MiB packet buffer (one per lane); "
+                                 "each lane's 64 MiB cube fits L2 (the lanes' cubes together do not) and is re-zeroed every window",
+                   "pipelining": f"{L} windows in flight: window k's update, detect and reset run in order on "
+                                 f"lane k mod {L} (its own stream, cube, workspaces and resident packet buffer), "
+                                 "overlapping the other lanes' windows",
+                   "lanes": L,
                    "parallelism": "one window per rank" if world > 1 else "single GPU",
                    **({"update_workspace_packets": args.workspace_packets} if args.workspace_packets else {})},
         "serial": {"ms_per_window": serial_ms, "value": n / (serial_ms * 1e-3) / 1e9, "unit": "Gpps",
@@ -1182,6 +1187,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="packets of the window the cpu_baseline oracle run takes (0: the whole window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=4,
+                    help="cbaa workload: windows in flight in the timed loop (at least 2), each on its own stream "
+                         "with its own cube, workspaces and packet buffer")
     ap.add_argument("--workspace-packets", type=int, default=0,
                     help="window workloads: size the update workspace for this many packets (0: the window); "
                          "fewer than a window makes the update run in several passes")
