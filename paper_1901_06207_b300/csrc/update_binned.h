@@ -108,7 +108,7 @@ inline uint32_t bin_ws_tables(const Geo &G, uint32_t n_cubes) {
 }
 
 // Words of the code buffer per packet a workspace is sized for: A codes
-// (column tiles), or a residual entry {iip, row} of the heavy split
+// (column tiles), or a residual entry {key, row} of the heavy split
 // (2 words) plus a record and an overflow entry of the row-tile pass.
 inline size_t bin_ws_words_per_pair(const Geo &G) { return (size_t)G.A + 2; }
 

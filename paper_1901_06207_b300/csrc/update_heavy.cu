@@ -20,7 +20,7 @@
 //   3. k_heavy_split  : every packet: a heavy source's row bit is set in
 //                       its bitmap in shared memory (a bit already set is
 //                       only read); any other packet is written out as
-//                       {iip, row}.  Each block ORs its bitmaps into the
+//                       {key, row} (the key: the bijection below of iip).  Each block ORs its bitmaps into the
 //                       global ones with one bulk reduction.
 //   4. the row-tile pass over the residual entries (update_rowtile.cu), whose
 //      counting kernel also ORs each heavy bitmap into the source's columns
@@ -292,18 +292,19 @@ __device__ __forceinline__ void st_pair_if(uint2 *ptr, uint32_t x, uint32_t y, u
 // The split of NP packets per lane of a warp (slot k of lane `lane`: a[k],
 // b[k], present when bit k of ok is set): rows and lookups; bitmap words of
 // the heavy ones (some word for the others), read together; sets of the bits
-// still clear; the others' entries {iip, row} (oriented) written to `region`
-// at places reserved with one shared-memory atomic per warp.  In phases, so
-// that the lanes' shared-memory reads are in flight together, and without
-// branches: every lane ORs (0 where nothing is to be set), the stores are
-// predicated.  bm_s: the shared
-// address of bm; kmask: heavy sources in bm - 1 (a power of two less one);
-// seed_fold: the row hash's seed folded for row_of_folded.
+// still clear; the others' entries {key, row} (oriented; key = heavy_key(iip),
+// a bijection) written to `region` at places reserved with one shared-memory
+// atomic per warp.  In phases, so that the lanes' shared-memory reads are in
+// flight together, and without branches: every lane ORs (0 where nothing is
+// to be set), the stores are predicated.  bm_s: the shared address of bm;
+// kmask: heavy sources in bm - 1 (a power of two less one); lw: log2 of the
+// words per bitmap (W); seed_fold: the row hash's seed folded for
+// row_of_folded.
 // FULL (every lane holds all NP packets, no inner network): the presence
 // bits are known to be set and are not tested.
 template <uint32_t NP, bool ORIENT, bool FULL>
 __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab, const uint32_t *bm, uint32_t bm_s,
-                                              uint32_t kmask, uint32_t seed_fold, uint32_t (&a)[NP],
+                                              uint32_t kmask, uint32_t lw, uint32_t seed_fold, uint32_t (&a)[NP],
                                               uint32_t (&b)[NP], uint32_t ok, uint2 *region, uint32_t *s_cnt,
                                               uint32_t lane) {
     static_assert(!(FULL && ORIENT), "orientation may drop packets");
@@ -313,20 +314,20 @@ __device__ __forceinline__ void split_packets(const Geo &G, const uint32_t *tab,
     for (uint32_t k = 0; k < NP; ++k) {
         if (ORIENT && ((ok >> k) & 1u) && !orient(G, a[k], b[k])) ok &= ~(1u << k);   // raw {src, dst} vs NI
         row[k] = row_of_folded(G, b[k], seed_fold);
-        e[k] = tab[heavy_key(a[k]) >> kHeavyTagBits];
+        a[k] = heavy_key(a[k]);                       // the key from here on (a bijection of iip)
+        e[k] = tab[a[k] >> kHeavyTagBits];
     }
-    // e ^ (key << 14) keeps only the index field exactly when the tags agree
-    // (key << 14 == a * (mul << 14) modulo 2^32); the empty marker's index
-    // field is all ones
+    // e ^ (key << 14) keeps only the index field exactly when the tags agree;
+    // the empty marker's index field is all ones
     uint32_t heavy = 0, wi[NP], wv[NP];
 #pragma unroll
     for (uint32_t k = 0; k < NP; ++k) {
-        const uint32_t d = e[k] ^ (a[k] * (kHeavyKeyMul << kHeavyTabBits));
+        const uint32_t d = e[k] ^ (a[k] << kHeavyTabBits);
         const bool hv = (FULL || ((ok >> k) & 1u)) && d < kHeavyIdxMask;
         heavy |= (uint32_t)hv << k;
-        // the bitmap word; for a packet that is not heavy some source's word (d & kmask
-        // < K), read and never set
-        wi[k] = (d & kmask) * G.W + (row[k] >> 5);
+        // the bitmap word (W = 2^lw words per source); for a packet that is not heavy some
+        // source's word (d & kmask < K), read and never set
+        wi[k] = ((d & kmask) << lw) + (row[k] >> 5);
         wv[k] = bm[wi[k]];
     }
     // a stale read only costs an atomic that changes nothing: every set is an OR
@@ -405,6 +406,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
     uint2 *region = resid + (uint64_t)blockIdx.x * rcap;
     const uint32_t bm_s = static_cast<uint32_t>(__cvta_generic_to_shared(bm));
     const uint32_t kmask = kwords / G.W - 1u;          // heavy sources held: a power of two
+    const uint32_t lw = __ffs(G.W) - 1u;               // W = g / 32 words per bitmap, a power of two
     const uint32_t seed_fold = G.seed_bv ^ (G.seed_bv >> 16);
     // chunk numbers fit 32 bits: a pass holds far fewer than 2^40 packets
     const uint32_t chunks = (uint32_t)((n + 255) / 256);
@@ -422,9 +424,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
             b[k] = (k & 1u) ? q[k / 2].w : q[k / 2].y;
         }
         if (!ORIENT && __all_sync(0xffffffffu, ok == 0xFFu))      // the same path for the whole warp
-            split_packets<8, false, true>(G, tab, bm, bm_s, kmask, seed_fold, a, b, ok, region, &s_cnt, lane);
+            split_packets<8, false, true>(G, tab, bm, bm_s, kmask, lw, seed_fold, a, b, ok, region, &s_cnt, lane);
         else
-            split_packets<8, ORIENT, false>(G, tab, bm, bm_s, kmask, seed_fold, a, b, ok, region, &s_cnt, lane);
+            split_packets<8, ORIENT, false>(G, tab, bm, bm_s, kmask, lw, seed_fold, a, b, ok, region, &s_cnt, lane);
 #pragma unroll
         for (uint32_t j = 0; j < 4; ++j) q[j] = qn[j];
         ok = okn;

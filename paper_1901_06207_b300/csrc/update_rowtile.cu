@@ -109,8 +109,8 @@ __device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
 constexpr uint32_t kCountTile = 4 * kCountThreads;
 
 // ORIENT (the cube has an inner network): packets are raw {src, dst} (orient()).
-// RESID: the input is the residual of the heavy split, entries {iip, row}
-// already oriented, one segment of regions of rcap entries whose first
+// RESID: the input is the residual of the heavy split, entries {key, row}
+// already oriented (key = heavy_key(iip), so iip = key * kHeavyKeyInv), one segment of regions of rcap entries whose first
 // rcount[r] are valid (rcap a multiple of every tile and block size).
 // samp > 1: only every samp-th tile of kCountTile packets is counted (a
 // sample for run capacities, see sample_capacity).  The first ncount blocks
@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
             for (int u = 0; u < 4; ++u) {
                 if (!RESID && ORIENT && !orient(G, ip[u], oip[u])) continue;      // raw {src, dst} against NI
                 const uint32_t row = RESID ? oip[u] : row_of(G, oip[u]);
-                atomicAdd(&hist[rb + row_tile(G, 0, mangle(G, ip[u]), row)], 1u);
+                const uint32_t iip = RESID ? ip[u] * kHeavyKeyInv : ip[u];
+                atomicAdd(&hist[rb + row_tile(G, 0, mangle(G, iip), row)], 1u);
             }
         } else {
             const uint64_t end = base + kCountTile < thi ? base + kCountTile : thi;
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kCountThreads) k_rt_count(const Geo G, const B
                 uint2 v = ld_pair(S.pairs[sp] + 2 * (p - S.start[sp]));
                 if (!RESID && ORIENT && !orient(G, v.x, v.y)) continue;
                 const uint32_t row = RESID ? v.y : row_of(G, v.y);
-                atomicAdd(&hist[row_tile(G, B.unit(S, sp), mangle(G, v.x), row)], 1u);
+                atomicAdd(&hist[row_tile(G, B.unit(S, sp), mangle(G, RESID ? v.x * kHeavyKeyInv : v.x), row)], 1u);
             }
         }
     }
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(THREADS, PPT > 8 ? 1 : (SHORT ? 2048 : 1536) /
         slot[k] = 0xFFFFFFFFu;
         if (rt[k] != 0xFFFFFFFFu) {
             if (!RESID && ORIENT && !orient(G, rec[k].x, rec[k].y)) continue;      // raw {src, dst} against NI
-            const uint32_t m = mangle(G, rec[k].x);
+            const uint32_t m = mangle(G, RESID ? rec[k].x * kHeavyKeyInv : rec[k].x);   // RESID: {key, row}
             const uint32_t row = RESID ? rec[k].y : row_of(G, rec[k].y);
             const uint32_t b = row_tile(G, rt[k], m, row);
             if (SHORT) rec[k].x = ((m >> G.r) << 5) | (row & 31u);
