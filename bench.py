@@ -1187,7 +1187,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="packets of the window the cpu_baseline oracle run takes (0: the whole window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--lanes", type=int, default=4,
+    ap.add_argument("--lanes", type=int, default=6,
                     help="cbaa workload: windows in flight in the timed loop (at least 2), each on its own stream "
                          "with its own cube, workspaces and packet buffer")
     ap.add_argument("--workspace-packets", type=int, default=0,
