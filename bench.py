@@ -677,11 +677,12 @@ def run_cbaa(args):
 
 
 def run_sharded(args):
-    """Every rank is an edge router with its own 64M-packet window.  Windows are double-buffered as in the
-    plain step: window k+1's reset and update (stream 1, cube k+1 mod 2) overlap window k's global-server
-    step (stream 2) -- the all-to-all of sketch slices, the OR of the owned ones, their restoration, the
-    device all-gather of every rank's host block and the merge by ip (ShardedDetector.enqueue: no host
-    wait).  Timed with CUDA events, max over ranks; value = packets of all ranks / step time."""
+    """Every rank is an edge router with its own 64M-packet window.  Window k's reset and update run on
+    lane k mod L (stream, cube, update workspace and packet buffer each) and overlap the other lanes'
+    updates and the earlier windows' global-server steps, which run on one stream in window order -- the
+    all-to-all of sketch slices, the OR of the owned ones, their restoration, the device all-gather of
+    every rank's host block and the merge by ip (ShardedDetector.enqueue: no host wait).  Timed with
+    CUDA events, max over ranks; value = packets of all ranks / step time."""
     import torch
     from paper_1901_06207_b300 import cbaa as C
     from paper_1901_06207_b300.shard import ShardedDetector
@@ -697,33 +698,41 @@ def run_sharded(args):
     pairs = torch.from_numpy(w.pairs.view(np.int32)).to(dev)
     if args.tuning:
         C.set_tuning(**json.loads(args.tuning))
-    cubes = [C.Cube(geo, device=dev) for _ in range(2)]
-    uws = C.UpdateWorkspace(geo, n, device=dev)
+    # Updates on `lanes` lanes (stream, cube, update workspace, packet buffer each), as in the plain
+    # step; the exchange and restoration of every window stay on one stream, in window order (the
+    # collectives of all ranks must be issued in one order), in the detector's two slots.
+    L = max(2, args.lanes)
+    cubes = [C.Cube(geo, device=dev) for _ in range(L)]
+    uwss = [C.UpdateWorkspace(geo, n, device=dev) for _ in range(L)]
+    lane_pairs = [pairs] + [pairs.clone() for _ in range(L - 1)]
     det = ShardedDetector(geo, theta, rank, world, device=dev)
     stream = torch.cuda.current_stream(dev)
-    s_up, s_det = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    done = [None, None]
+    s_ups, s_det = [torch.cuda.Stream(dev) for _ in range(L)], torch.cuda.Stream(dev)
+    done = [None] * L
 
     def step(k):
-        b = k & 1
-        with torch.cuda.stream(s_up):
+        b = k % L
+        su = s_ups[b]
+        with torch.cuda.stream(su):
             if done[b] is not None:
-                s_up.wait_event(done[b])          # its previous window's exchange has read the cube
+                su.wait_event(done[b])            # its previous window's exchange has read the cube
             cubes[b].reset()
-            cubes[b].update_binned(pairs, uws)
+            cubes[b].update_binned(lane_pairs[b], uwss[b])
             up = torch.cuda.Event()
-            up.record(s_up)
+            up.record(su)
         with torch.cuda.stream(s_det):
             s_det.wait_event(up)
-            det.enqueue(cubes[b], b)
+            det.enqueue(cubes[b], k & 1)
             done[b] = torch.cuda.Event()
             done[b].record(s_det)
 
     def join():
-        stream.wait_stream(s_up)
+        for su in s_ups:
+            stream.wait_stream(su)
         stream.wait_stream(s_det)
 
-    s_up.wait_stream(stream)
+    for su in s_ups:
+        su.wait_stream(stream)
     s_det.wait_stream(stream)
     for k in range(max(args.warmup, 3)):
         step(k)
@@ -735,7 +744,8 @@ def run_sharded(args):
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         t_start.record(stream)
-        s_up.wait_stream(stream)
+        for su in s_ups:
+            su.wait_stream(stream)
         s_det.wait_stream(stream)
         for k in range(steps):
             step(k)
@@ -753,9 +763,12 @@ def run_sharded(args):
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {**desc, "workload": "sharded_64m_per_rank",
-                       "step": "double-buffered: a window's reset and update (stream 1) overlap the previous "
-                               "window's all-to-all of sketch slices, OR of the owned ones, restoration, "
-                               "device all-gather of the host blocks and merge by ip (stream 2); no host wait",
+                       "step": f"window k's reset and update on lane k mod {L} (its own stream, cube, update "
+                               "workspace and packet buffer) overlap the other lanes' updates and the earlier "
+                               "windows' all-to-all of sketch slices, OR of the owned ones, restoration, device "
+                               "all-gather of the host blocks and merge by ip (one exchange stream, window "
+                               "order); no host wait",
+                       "lanes": L,
                        "parallelism": f"{world} ranks, sketches split {1 << geo['r']} / {world}"},
             "all_to_all_bytes_per_rank": {"sent": 4 * words * (world - 1) // world,
                                           "received": 4 * words * (world - 1) // world},
