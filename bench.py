@@ -511,7 +511,34 @@ def run_cbaa(args):
         if rep:
             zc_ms.append(e0.elapsed_time(e1))
 
-    # timed region: double-buffered windows
+    # The split's grid for windows in flight: the autotuner picks shapes for one window alone, where
+    # one split block per SM is fastest; with windows in flight, a split on fewer SMs leaves the rest
+    # to the other lanes' kernels.  A short sweep of the lanes loop picks the grid (results never
+    # depend on it); the serial figures above keep one block per SM.
+    serial_tuning = C.get_tuning()
+    lanes_sweep = {}
+    if uws is not None and args.lanes_split_sweep:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        for eighths in (8, 6, 4, 3, 2, 1):
+            C.set_tuning(**{**serial_tuning, "split_blocks": 0 if eighths == 8 else sms * eighths // 8})
+            for k in range(2 * L):
+                piped_step(k)
+            join_streams()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for su in lane_stream:
+                su.wait_stream(stream)
+            for k in range(4 * L):
+                piped_step(k)
+            join_streams()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lanes_sweep[C.get_tuning()["split_blocks"]] = e0.elapsed_time(e1) / (4 * L)
+        best = reduce_over_ranks(float(min(lanes_sweep, key=lanes_sweep.get)), world, "max", dev)
+        C.set_tuning(**{**serial_tuning, "split_blocks": int(best)})
+    lanes_tuning = C.get_tuning()
+
+    # timed region: windows in flight on the lanes
     for k in range(max(args.warmup, 0)):
         piped_step(k)
     join_streams()
@@ -535,6 +562,7 @@ def run_cbaa(args):
         assert inf2["status"] == C.OK and inf2["n_hosts"] == inf["n_hosts"], (inf2, inf)
     packets_all = reduce_over_ranks(float(n), world, "sum", dev)
     value = packets_all * args.steps / (total_ms_max * 1e-3) / 1e9
+    C.set_tuning(**serial_tuning)
 
     # end to end through the public API with host buffers, windows pipelined
     # on three streams: H2D of window k+1's packets from pinned memory (s_copy)
@@ -630,7 +658,11 @@ def run_cbaa(args):
         "autotune": None if tuned is None else {
             "pick": tuned["path"], "tuning": tuned["tuning"], "best_ms": tuned["ms"],
             "worst_ms": tuned["worst_ms"], "candidates": tuned["candidates"]},
-        "tuning": C.get_tuning(),
+        "tuning": serial_tuning,
+        "lanes_tuning": {"tuning": lanes_tuning,
+                         "split_sweep_ms_per_window": {str(k): v for k, v in lanes_sweep.items()},
+                         "note": "the timed region's shapes: the autotuner's pick with the split grid "
+                                 "(split_blocks, 0 = one block per SM) chosen by timing the lanes loop"},
         "roofline": {"bound": "hbm", "kernel": f"update ({path}: " +
                      ({7: "heavy sample+hist+split (selection in each split block), residual count (with the "
                          "heavy bitmaps' expansion)+scan+scatter+apply",
@@ -1203,6 +1235,9 @@ def main():
     ap.add_argument("--lanes", type=int, default=6,
                     help="cbaa workload: windows in flight in the timed loop (at least 2), each on its own stream "
                          "with its own cube, workspaces and packet buffer")
+    ap.add_argument("--no-lanes-split-sweep", dest="lanes_split_sweep", action="store_false",
+                    help="cbaa workload: keep the tuning's split grid in the timed region instead of timing "
+                         "the lanes loop at 8/8 .. 1/8 of the SMs")
     ap.add_argument("--workspace-packets", type=int, default=0,
                     help="window workloads: size the update workspace for this many packets (0: the window); "
                          "fewer than a window makes the update run in several passes")

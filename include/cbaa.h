@@ -131,6 +131,10 @@ typedef struct cbaa_tuning {
                                       the rest through row tiles.  0 = on for passes of >= 4Mi packets
                                       (128 KiB of bitmaps per block), 1 = off, 2 = on with 64 KiB of bitmaps
                                       (half as many sources), 3 = on with 128 KiB */
+    uint32_t split_blocks;         /* heavy-source split: blocks of 1024 threads (at most one per SM),
+                                      0 = one per SM (the shortest update).  Fewer leave SMs free for
+                                      kernels on other streams, e.g. other windows' updates and detects in
+                                      flight, at the cost of this update's time; at most 4096 */
 } cbaa_tuning;
 
 typedef struct cbaa_cube cbaa_cube;   /* opaque handle: a params copy plus the caller's memory */

@@ -53,7 +53,7 @@ class InnerNet(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("scatter_shape", ctypes.c_uint32), ("count_blocks_per_sm", ctypes.c_uint32),
                 ("apply_items_per_sm", ctypes.c_uint32), ("direct_blocks_per_sm", ctypes.c_uint32),
-                ("tile_kind", ctypes.c_uint32), ("heavy", ctypes.c_uint32)]
+                ("tile_kind", ctypes.c_uint32), ("heavy", ctypes.c_uint32), ("split_blocks", ctypes.c_uint32)]
 
 
 HOST_DTYPE = np.dtype([("ip", "<u4"), ("z", "<u4"), ("est", "<f4"), ("flags", "<u4")])
@@ -227,8 +227,9 @@ def update_multi_workspace_bytes(d: dict, n_cubes: int, max_pairs: int) -> int:
 
 
 def set_tuning(scatter_shape=0, count_blocks_per_sm=0, apply_items_per_sm=0, direct_blocks_per_sm=0, tile_kind=0,
-               heavy=0):
-    t = Tuning(scatter_shape, count_blocks_per_sm, apply_items_per_sm, direct_blocks_per_sm, tile_kind, heavy)
+               heavy=0, split_blocks=0):
+    t = Tuning(scatter_shape, count_blocks_per_sm, apply_items_per_sm, direct_blocks_per_sm, tile_kind, heavy,
+               split_blocks)
     _check(lib().cbaa_set_tuning(ctypes.byref(t)), "set_tuning")
 
 

@@ -294,7 +294,7 @@ int cbaa_cube_update_binned(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n
 
 int cbaa_set_tuning(const cbaa_tuning *t) {
     if (!t || t->scatter_shape > 8 || t->count_blocks_per_sm > 64 || t->apply_items_per_sm > 1024 ||
-        t->direct_blocks_per_sm > 64 || t->tile_kind > 3 || t->heavy > 3)
+        t->direct_blocks_per_sm > 64 || t->tile_kind > 3 || t->heavy > 3 || t->split_blocks > 4096)
         return CBAA_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_tuning_mu);
     g_tuning = *t;

@@ -457,6 +457,7 @@ Residual residual_layout(const cbaa_tuning &T, uint64_t m, const uint32_t *entri
     const uint64_t wpb = sh.threads / 32;
     // at least a region's worth of packets per block, so that rounding regions up wastes little
     uint64_t blocks = (uint64_t)num_sms() * sh.per_sm;
+    if (T.split_blocks && T.split_blocks < blocks) blocks = T.split_blocks;      // SMs left to other streams
     const uint64_t need = (m + kHeavyRegionAlign - 1) / kHeavyRegionAlign;
     if (need < blocks) blocks = need;
     if (blocks > kHeavyMaxRegions) blocks = kHeavyMaxRegions;

@@ -115,9 +115,11 @@ def test_update_workspace_limits(C):
 def test_tuning_roundtrip_and_limits(C):
     before = C.get_tuning()
     C.set_tuning(scatter_shape=3, count_blocks_per_sm=4, apply_items_per_sm=16, direct_blocks_per_sm=2,
-                 tile_kind=1, heavy=2)
+                 tile_kind=1, heavy=2, split_blocks=74)
     assert C.get_tuning() == dict(scatter_shape=3, count_blocks_per_sm=4, apply_items_per_sm=16,
-                                  direct_blocks_per_sm=2, tile_kind=1, heavy=2)
+                                  direct_blocks_per_sm=2, tile_kind=1, heavy=2, split_blocks=74)
+    with pytest.raises(C.CbaaError):
+        C.set_tuning(split_blocks=4097)
     with pytest.raises(C.CbaaError):
         C.set_tuning(tile_kind=4)
     with pytest.raises(C.CbaaError):

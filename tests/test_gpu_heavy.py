@@ -101,6 +101,17 @@ def test_heavy_split_passes_and_unaligned_start(C, oracle, heavy):
     assert np.array_equal(got, oracle.build_cube(d, pairs[1:]))
 
 
+@pytest.mark.parametrize("split_blocks", [1, 37, 74, 4096])
+@pytest.mark.parametrize("win", ["4m", "tiny"])
+def test_heavy_split_fewer_blocks(C, oracle, win, split_blocks):
+    """The split's grid held below one block per SM (SMs left to other streams): larger residual
+    regions per block, one block for the whole window; 4096 is capped at one block per SM."""
+    d = GEO.L2
+    pairs = pairs_of(win)
+    got = _run(C, d, pairs, dict(heavy=3, tile_kind=3, split_blocks=split_blocks))
+    assert np.array_equal(got, oracle.build_cube(d, pairs))
+
+
 @pytest.mark.parametrize("heavy", [2, 3])
 def test_heavy_split_skewed(C, oracle, heavy):
     """Half the packets one pair and a fifth one source to many peers (one source dominates the
