@@ -1212,7 +1212,8 @@ def run_serve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 1000 windows for the window workloads on the GPU, 200 otherwise)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cbaa", "reference"], default="cbaa")
     ap.add_argument("--workload", default="window64m",
@@ -1249,6 +1250,8 @@ def main():
     ap.add_argument("--learned-size", default="full", choices=["full", "scaled"],
                     help="learned workload: 256M-packet windows (full) or 64M with the same column load")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 1000 if args.impl == "cbaa" and args.workload in ("window64m", "window1m") else 200
     if args.warmup < 3 and args.impl == "cbaa":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
