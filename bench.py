@@ -194,6 +194,28 @@ def reduce_over_ranks(x: float, world: int, op: str, device=None) -> float:
 
 # ----------------------------------------------------------------------------- CPU oracle leg
 
+def sweep_split_grid(C, base_tuning: dict, run_windows, lanes: int, world: int, dev):
+    """The heavy split's grid for windows in flight: time `run_windows(count)` (windows through the
+    lanes loop, streams joined to the current stream) with the split on 8/8, 6/8, 4/8, 3/8, 2/8 and
+    1/8 of the SMs and set the fastest (the same on every rank).  Returns {split_blocks: ms/window}."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream(dev)
+    times = {}
+    for eighths in (8, 6, 4, 3, 2, 1):
+        C.set_tuning(**{**base_tuning, "split_blocks": 0 if eighths == 8 else max(1, sms * eighths // 8)})
+        run_windows(2 * lanes)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run_windows(4 * lanes)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[C.get_tuning()["split_blocks"]] = e0.elapsed_time(e1) / (4 * lanes)
+    best = reduce_over_ranks(float(min(times, key=times.get)), world, "max", dev)
+    C.set_tuning(**{**base_tuning, "split_blocks": int(best)})
+    return times
+
+
 def oracle_sample(geo, pairs: np.ndarray, theta: int, n_sample: int):
     """Time the plain CPU oracle (single thread) on the first n_sample packets + one detect."""
     from oracle import oracle as O
@@ -517,25 +539,16 @@ def run_cbaa(args):
     # depend on it); the serial figures above keep one block per SM.
     serial_tuning = C.get_tuning()
     lanes_sweep = {}
+
+    def run_windows(count):
+        for su in lane_stream:
+            su.wait_stream(stream)
+        for k in range(count):
+            piped_step(k)
+        join_streams()
+
     if uws is not None and args.lanes_split_sweep:
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        for eighths in (8, 6, 4, 3, 2, 1):
-            C.set_tuning(**{**serial_tuning, "split_blocks": 0 if eighths == 8 else sms * eighths // 8})
-            for k in range(2 * L):
-                piped_step(k)
-            join_streams()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for su in lane_stream:
-                su.wait_stream(stream)
-            for k in range(4 * L):
-                piped_step(k)
-            join_streams()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            lanes_sweep[C.get_tuning()["split_blocks"]] = e0.elapsed_time(e1) / (4 * L)
-        best = reduce_over_ranks(float(min(lanes_sweep, key=lanes_sweep.get)), world, "max", dev)
-        C.set_tuning(**{**serial_tuning, "split_blocks": int(best)})
+        lanes_sweep = sweep_split_grid(C, serial_tuning, run_windows, L, world, dev)
     lanes_tuning = C.get_tuning()
 
     # timed region: windows in flight on the lanes
@@ -770,6 +783,16 @@ def run_sharded(args):
         step(k)
     join()
     torch.cuda.synchronize()
+
+    def run_windows(count):
+        for su in s_ups:
+            su.wait_stream(stream)
+        s_det.wait_stream(stream)
+        for k in range(count):
+            step(k)
+        join()
+
+    split_sweep = sweep_split_grid(C, C.get_tuning(), run_windows, L, world, dev) if args.lanes_split_sweep else {}
     steps = max(1, min(args.steps, 200))
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
@@ -796,12 +819,15 @@ def run_sharded(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {**desc, "workload": "sharded_64m_per_rank",
                        "step": f"window k's reset and update on lane k mod {L} (its own stream, cube, update "
-                               "workspace and packet buffer) overlap the other lanes' updates and the earlier "
+                               "workspace and packet buffer; the split's grid from a timed sweep) overlap the "
+                               "other lanes' updates and the earlier "
                                "windows' all-to-all of sketch slices, OR of the owned ones, restoration, device "
                                "all-gather of the host blocks and merge by ip (one exchange stream, window "
                                "order); no host wait",
                        "lanes": L,
                        "parallelism": f"{world} ranks, sketches split {1 << geo['r']} / {world}"},
+            "tuning": C.get_tuning(),
+            "split_sweep_ms_per_window": {str(k): v for k, v in split_sweep.items()},
             "all_to_all_bytes_per_rank": {"sent": 4 * words * (world - 1) // world,
                                           "received": 4 * words * (world - 1) // world},
             "hosts_detected": int(hosts.size),
