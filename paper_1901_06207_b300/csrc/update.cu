@@ -146,16 +146,12 @@ __device__ void eps_zmax_of(const Geo &G, const unsigned long long *za, double E
 // ---------------------------------------------------------------------------
 // Zero counts.  Block (cs*A + a, split) walks a slice of array a of sketch
 // cs.  TPC threads share one column, each summing the popcounts of its
-// PER 16-byte pieces (TPC = W/(4 ZC_PIECES) clamped to [1, 32], so a
-// thread has ZC_PIECES pieces of a column when the column is long enough),
-// then the TPC lanes reduce by shuffles.  ZC_U columns per thread group are
+// PER 16-byte pieces (TPC = W/(4 kZcPieces) clamped to [1, 32], so a
+// thread has kZcPieces pieces of a column when the column is long enough),
+// then the TPC lanes reduce by shuffles.  kZcU columns per thread group are
 // in flight.  One atomic per block adds the slice's zeros to za[cs][a].
-#ifndef ZC_PIECES
-#define ZC_PIECES 4
-#endif
-#ifndef ZC_U
-#define ZC_U 2
-#endif
+constexpr uint32_t kZcPieces = 4;
+constexpr uint32_t kZcU = 2;
 
 // With `done` set, the last block to finish also computes eps and Zmax of the
 // sketches [cs_lo, cs_hi) (one launch fewer in the detect); done counts the
@@ -172,7 +168,7 @@ __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t
     const uint32_t c0 = (uint32_t)(((uint64_t)ncol * blockIdx.y) / splits);
     const uint32_t c1 = (uint32_t)(((uint64_t)ncol * (blockIdx.y + 1)) / splits);
     const uint32_t q = G.W / 4;                      // 16-byte pieces per column
-    const uint32_t t0 = q / ZC_PIECES;
+    const uint32_t t0 = q / kZcPieces;
     const uint32_t tpc = t0 < 1 ? 1 : (t0 > 32 ? 32 : t0);
     const uint32_t per = q / tpc;                    // pieces per thread
     const uint32_t sub = threadIdx.x % tpc;
@@ -180,7 +176,7 @@ __global__ void __launch_bounds__(256) k_zero_counts(const Geo G, const uint32_t
     const uint4 *arr4 = reinterpret_cast<const uint4 *>(cube + (size_t)cs * G.cs_words + G.arr_base[a]);
 
     unsigned long long acc = 0;
-    constexpr uint32_t U = ZC_U;
+    constexpr uint32_t U = kZcU;
     for (uint32_t base = c0; base < c1; base += U * cols_per_iter) {
         uint32_t ones[U];
 #pragma unroll
