@@ -397,23 +397,27 @@ def run_cbaa(args):
     kernels_per_step = -(-n // pass_n) * update_kernels(uws is not None, C.get_tuning(), pass_n) + \
         detect_kernels(geo)
 
-    def do_update(c=None, src=None, u=None):
+    def do_update(c=None, src=None, u=None, assign=False):
+        """assign: the cube becomes this window's bits alone (no reset before)."""
         c = cube if c is None else c
         src = pairs_dev if src is None else src
         u = uws if u is None else u
         if u is not None:
-            c.update_binned(src, u)
+            c.update_binned(src, u, assign=assign)
         else:
+            if assign:
+                c.reset()
             c.update(src)
 
     # Windows in flight on `lanes` lanes, as a deployed detector runs them when
     # windows close faster than one window's update and detect take: lane j
     # owns a stream, a cube, an update workspace, a detect workspace, its
     # outputs and its own resident packet buffer; window k runs on lane
-    # k mod L as update, detect, reset in stream order, so that different
-    # windows' kernels overlap (one window's heavy split beside another's
-    # residual kernels and a third's detect).  Every window is fully updated
-    # and detected.
+    # k mod L as an assigning update (the lane's previous window discarded:
+    # the split's blocks zero the cube, no reset) and a detect, in stream
+    # order, so that different windows' kernels overlap (one window's heavy
+    # split beside another's residual kernels and a third's detect).  Every
+    # window is fully updated and detected.
     L = max(2, args.lanes)
     lane_cube = [cube] + [C.Cube(geo, device=dev) for _ in range(L - 1)]
     lane_uws = [uws] + [C.UpdateWorkspace(geo, args.workspace_packets or n, device=dev) if uws is not None else None
@@ -427,13 +431,10 @@ def run_cbaa(args):
 
     def piped_step(k):
         b = k % L
+        lane_fresh[b] = False
         with torch.cuda.stream(lane_stream[b]):
-            if lane_fresh[b]:
-                lane_cube[b].reset()
-                lane_fresh[b] = False
-            do_update(lane_cube[b], lane_pairs[b], lane_uws[b])
+            do_update(lane_cube[b], lane_pairs[b], lane_uws[b], assign=True)
             lane_cube[b].detect_async(theta, lane_ws[b], lane_out[b], lane_info[b])
-            lane_cube[b].reset()                  # the lane's next window starts empty
 
     def join_streams():
         for su in lane_stream:
@@ -646,7 +647,8 @@ def run_cbaa(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {**desc, "l2": f"inputs larger than L2: each step streams a {8 * n >> 20} MiB packet buffer (one per lane); "
                                  "each lane's 64 MiB cube fits L2 (the lanes' cubes together do not) and is re-zeroed every window",
-                   "pipelining": f"{L} windows in flight: window k's update, detect and reset run in order on "
+                   "pipelining": f"{L} windows in flight: window k's assigning update (the lane's previous "
+                                 "window discarded inside the update, no reset) and detect run in order on "
                                  f"lane k mod {L} (its own stream, cube, workspaces and resident packet buffer), "
                                  "overlapping the other lanes' windows",
                    "lanes": L,
@@ -722,9 +724,10 @@ def run_cbaa(args):
 
 
 def run_sharded(args):
-    """Every rank is an edge router with its own 64M-packet window.  Window k's reset and update run on
-    lane k mod L (stream, cube, update workspace and packet buffer each) and overlap the other lanes'
-    updates and the earlier windows' global-server steps, which run on one stream in window order -- the
+    """Every rank is an edge router with its own 64M-packet window.  Window k's assigning update (its
+    lane's previous window discarded inside the update) runs on lane k mod L (stream, cube, update
+    workspace and packet buffer each) and overlaps the other lanes' updates and the earlier windows'
+    global-server steps, which run on one stream in window order -- the
     all-to-all of sketch slices, the OR of the owned ones, their restoration, the device all-gather of
     every rank's host block and the merge by ip (ShardedDetector.enqueue: no host wait).  Timed with
     CUDA events, max over ranks; value = packets of all ranks / step time."""
@@ -761,8 +764,7 @@ def run_sharded(args):
         with torch.cuda.stream(su):
             if done[b] is not None:
                 su.wait_event(done[b])            # its previous window's exchange has read the cube
-            cubes[b].reset()
-            cubes[b].update_binned(lane_pairs[b], uwss[b])
+            cubes[b].update_binned(lane_pairs[b], uwss[b], assign=True)     # no reset: the update replaces it
             up = torch.cuda.Event()
             up.record(su)
         with torch.cuda.stream(s_det):
@@ -818,7 +820,7 @@ def run_sharded(args):
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {**desc, "workload": "sharded_64m_per_rank",
-                       "step": f"window k's reset and update on lane k mod {L} (its own stream, cube, update "
+                       "step": f"window k's assigning update on lane k mod {L} (its own stream, cube, update "
                                "workspace and packet buffer; the split's grid from a timed sweep) overlap the "
                                "other lanes' updates and the earlier "
                                "windows' all-to-all of sketch slices, OR of the owned ones, restoration, device "

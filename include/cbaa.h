@@ -216,6 +216,18 @@ size_t cbaa_update_workspace_bytes(const cbaa_params *p, size_t max_pairs);
 int cbaa_cube_update_binned(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *dev_ws, size_t ws_bytes,
                             void *stream);
 
+/* The same as cbaa_cube_update_binned, except that the cube's words become
+ * the bits of these n packets alone: its previous content is discarded, so
+ * no cbaa_cube_reset is needed first (a window's first batch; the windows'
+ * cube reused without a reset in between).  Where the heavy-source split
+ * serves the pass (one cube, row tiles; see cbaa_tuning.heavy), the split's
+ * blocks zero the cube while they read the packets (nothing writes the cube
+ * before the split ends); on the other paths the cube is zeroed first by a
+ * memset.  n = 0 zeroes the cube.  Errors as cbaa_cube_update_binned; on an
+ * error nothing is enqueued. */
+int cbaa_cube_update_binned_assign(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *dev_ws,
+                                   size_t ws_bytes, void *stream);
+
 /* Workspace for cbaa_cube_update_multi with n_cubes cubes of geometry p
  * and up to max_pairs packets per pass (0 if invalid, n_cubes > 16, or the
  * cubes together exceed 512 MiB).  Host only. */

@@ -98,6 +98,7 @@ def _signatures():
         "cbaa_detect_static": (ctypes.c_int, [vp, ctypes.c_uint32, vp, sz, vp, vp]),
         "cbaa_update_workspace_bytes": (sz, [P, sz]),
         "cbaa_cube_update_binned": (ctypes.c_int, [vp, vp, sz, vp, sz, vp]),
+        "cbaa_cube_update_binned_assign": (ctypes.c_int, [vp, vp, sz, vp, sz, vp]),
         "cbaa_update_multi_workspace_bytes": (sz, [P, ctypes.c_int, sz]),
         "cbaa_cube_update_multi": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                                   ctypes.POINTER(sz), vp, sz, vp]),
@@ -331,15 +332,17 @@ class Cube:
     def update_ptr(self, ptr: int, n: int, stream=None):
         _check(lib().cbaa_cube_update(self.handle, ptr, n, _stream_ptr(stream)), "cube_update")
 
-    def update_binned(self, pairs, ws: "UpdateWorkspace", n: int | None = None, stream=None):
-        """Partitioned Alg. 1 (same bits as update) using an UpdateWorkspace."""
+    def update_binned(self, pairs, ws: "UpdateWorkspace", n: int | None = None, stream=None, assign: bool = False):
+        """Partitioned Alg. 1 (same bits as update) using an UpdateWorkspace; assign=True: the cube
+        becomes these packets' bits alone (no reset needed first)."""
         if n is None:
             n = pairs.shape[0] if pairs.dim() == 2 else pairs.numel() // 2
-        self.update_binned_ptr(pairs.data_ptr(), n, ws, stream)
+        self.update_binned_ptr(pairs.data_ptr(), n, ws, stream, assign)
 
-    def update_binned_ptr(self, ptr: int, n: int, ws: "UpdateWorkspace", stream=None):
-        _check(lib().cbaa_cube_update_binned(self.handle, ptr, n, ws.ptr, ws.nbytes, _stream_ptr(stream)),
-               "cube_update_binned")
+    def update_binned_ptr(self, ptr: int, n: int, ws: "UpdateWorkspace", stream=None, assign: bool = False):
+        fn = lib().cbaa_cube_update_binned_assign if assign else lib().cbaa_cube_update_binned
+        _check(fn(self.handle, ptr, n, ws.ptr, ws.nbytes, _stream_ptr(stream)),
+               "cube_update_binned_assign" if assign else "cube_update_binned")
 
     def merge(self, others, stream=None, assign: bool = False):
         """self |= OR(others); assign=True: self = OR(others) without reading self (no reset needed)."""

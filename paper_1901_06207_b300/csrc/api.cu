@@ -220,8 +220,9 @@ size_t cbaa_update_multi_workspace_bytes(const cbaa_params *p, int n_cubes, size
 namespace {
 
 // cbaa_cube_update_multi, and with `global` set cbaa_cube_update_multi_merge.
+// assign (one cube only): the cube's words become the pass's bits alone.
 int update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *dev_pairs, const size_t *n,
-                 cbaa_cube *global, void *dev_ws, size_t ws_bytes, void *stream) {
+                 cbaa_cube *global, void *dev_ws, size_t ws_bytes, void *stream, bool assign = false) {
     if (!cubes || !dev_pairs || !n || n_cubes < 1 || n_cubes > (int)cbaa::kMaxRouters) return CBAA_ERR_INVALID_ARG;
     if (!dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 15u)) return CBAA_ERR_INVALID_ARG;
     const cbaa_cube *c0 = cubes[0];
@@ -264,7 +265,8 @@ int update_multi(cbaa_cube *const *cubes, int n_cubes, const uint32_t *const *de
     if (total == 0) return CBAA_OK;
     cbaa::BinWs W;
     if (!cbaa::bin_ws_make(G, (uint32_t)n_cubes, dev_ws, ws_bytes, &W)) return CBAA_ERR_INVALID_ARG;
-    return cuda_status(cbaa::launch_update_segments(G, S, total, W, current_tuning(), as_stream(stream)));
+    return cuda_status(cbaa::launch_update_segments(G, S, total, W, current_tuning(), as_stream(stream),
+                                                    assign && n_cubes == 1));
 }
 
 }  // namespace
@@ -290,6 +292,16 @@ int cbaa_cube_update_binned(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n
     const uint32_t *pp[1] = {dev_pairs};
     const size_t nn[1] = {n};
     return cbaa_cube_update_multi(cubes, 1, pp, nn, dev_ws, ws_bytes, stream);
+}
+
+int cbaa_cube_update_binned_assign(cbaa_cube *cube, const uint32_t *dev_pairs, size_t n, void *dev_ws,
+                                   size_t ws_bytes, void *stream) {
+    if (!cube) return CBAA_ERR_INVALID_ARG;
+    if (n == 0) return cuda_status(cudaMemsetAsync(cube->data, 0, cube->bytes, as_stream(stream)));
+    cbaa_cube *cubes[1] = {cube};
+    const uint32_t *pp[1] = {dev_pairs};
+    const size_t nn[1] = {n};
+    return update_multi(cubes, 1, pp, nn, nullptr, dev_ws, ws_bytes, stream, true);
 }
 
 int cbaa_set_tuning(const cbaa_tuning *t) {

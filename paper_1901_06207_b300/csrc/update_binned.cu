@@ -379,10 +379,14 @@ cudaError_t launch_bin_scan(uint32_t *counts, uint32_t nb, uint32_t ch, const Bi
 }
 
 cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, bool assign) {
     if (n == 0) return cudaSuccess;
     if (S.k == 1 && !S.merge && heavy_enabled(G, S.n_routers, n, T))
-        return launch_update_heavy(G, S.cube[S.router[0]], S.pairs[0], n, W, T, s);
+        return launch_update_heavy(G, S.cube[S.router[0]], S.pairs[0], n, W, T, s, assign);
+    if (assign && S.n_routers == 1) {
+        const cudaError_t e = cudaMemsetAsync(S.cube[0], 0, G.cube_words * 4u, s);
+        if (e != cudaSuccess) return e;
+    }
     if (T.tile_kind != 1 && rowtile_ok(G, S.n_routers)) return launch_update_rowtile(G, S, n, W, T, s);
     if (G.n_ra == 3 && G.n_va == 1) return launch_binned_t<3, 1>(G, S, n, W, T, s);
     return launch_binned_t<0, 0>(G, S, n, W, T, s);

@@ -151,13 +151,12 @@ inline bool bin_ws_make(const Geo &G, uint32_t n_cubes, void *base, size_t bytes
     return true;
 }
 
+// assign (one cube): the cube's words become the pass's bits alone (zeroed
+// by the heavy split's blocks, or by a memset first on the other paths).
 cudaError_t launch_update_segments(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool assign = false);
 cudaError_t launch_update_rowtile(const Geo &G, const BinSegs &S, uint64_t n, const BinWs &W, const cbaa_tuning &T,
                                   cudaStream_t s);
-// Residual of the heavy split: region b holds rcount[b] entries {mangled
-// ip, row} from entry b * rcap on (rcap a multiple of kHeavyRegionAlign),
-// nreg regions.
 // Source key of an inner address, by which the heavy split looks sources up:
 // x * an odd constant is a bijection of the 32-bit words, and its top bits mix
 // all bits of x (Knuth's multiplicative hashing).  The expansion turns a key
@@ -205,6 +204,8 @@ __device__ __forceinline__ void heavy_expand_part(const Geo &G, uint32_t *cube, 
 }
 #endif
 
+// Residual of the heavy split: region b holds rcount[b] entries {key, row}
+// from entry b * rcap on (rcap a multiple of kHeavyRegionAlign), nreg regions.
 struct Residual {
     const uint2 *entries;
     const uint32_t *rcount;
@@ -223,8 +224,9 @@ cudaError_t rowtile_pass_residual(const Geo &G, uint32_t *cube, const Residual &
 uint64_t rowtile_pass_words(const Geo &G, uint64_t m, bool sampled);
 constexpr uint64_t kRowTileMinSampled = 8ull << 20;  // below this every packet is counted
 // Heavy-source split in front of the row tiles (single cube, update_heavy.cu).
+// assign: the split's blocks of the first pass zero the cube first.
 cudaError_t launch_update_heavy(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint64_t n, const BinWs &W,
-                                const cbaa_tuning &T, cudaStream_t s);
+                                const cbaa_tuning &T, cudaStream_t s, bool assign = false);
 // Whether the split serves a pass over these cubes with this tuning.
 bool heavy_enabled(const Geo &G, uint32_t n_cubes, uint64_t n, const cbaa_tuning &T);
 cudaError_t launch_bin_scan(uint32_t *counts, uint32_t nb, uint32_t ch, const BinWs &W, cudaStream_t s,

@@ -381,7 +381,9 @@ __device__ __forceinline__ void split_flush(const uint32_t *bm, uint32_t kwords,
 // Every warp walks its own chunks of 256 packets (chunk c for c = global
 // warp, + all warps, ...), the next chunk's 16-byte loads in flight in
 // registers while it works on the current one (two register sets used in
-// turn, so nothing is copied between them).  Shared memory: the lookup
+// turn, so nothing is copied between them).  zero (an assigning update's
+// first pass): the blocks first zero the cube's zq 16-byte words, which no
+// kernel before the split's end reads or writes.  Shared memory: the lookup
 // table (built by split_select), then K row bitmaps of W words (kwords
 // words).  Residual entries go
 // to this block's region (rcap entries from blockIdx.x * rcap), one
@@ -394,7 +396,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
                                                                uint32_t kwords, uint32_t *__restrict__ bits_g,
                                                                uint32_t *__restrict__ list, uint32_t *__restrict__ ctr,
                                                                uint2 *__restrict__ resid, uint64_t rcap,
-                                                               uint32_t *__restrict__ rcount) {
+                                                               uint32_t *__restrict__ rcount, uint4 *__restrict__ zero,
+                                                               uint64_t zq) {
     extern __shared__ __align__(16) uint32_t sm[];
     uint32_t *tab = sm;
     uint32_t *bm = sm + kTabWords;
@@ -415,7 +418,19 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
     uint32_t c = blockIdx.x * (THREADS / 32) + (tid >> 5);
     uint4 q[4], qn[4];
     uint32_t ok = c < chunks ? split_load(pairs, n, c, lane, full, q) : 0u;
+    // the cube's zeroing spread over the chunk loop: one 16-byte store per thread every
+    // zevery chunks, the rest after the loop
+    const uint64_t zstride = (uint64_t)gridDim.x * THREADS;
+    uint64_t zi = (uint64_t)blockIdx.x * THREADS + tid;
+    const uint32_t wchunks = (chunks + nw - 1) / nw, zper = (uint32_t)((zq + zstride - 1) / zstride);
+    const uint32_t zevery = zper ? (wchunks / zper > 1 ? wchunks / zper : 1) : 0xFFFFFFFFu;
+    uint32_t zt = 0;
     for (; c < chunks; c += nw) {
+        if (++zt >= zevery && zi < zq) {
+            zero[zi] = make_uint4(0u, 0u, 0u, 0u);
+            zi += zstride;
+            zt = 0;
+        }
         const uint32_t okn = c + nw < chunks ? split_load(pairs, n, c + nw, lane, full, qn) : 0u;
         uint32_t a[8], b[8];
 #pragma unroll
@@ -431,6 +446,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_heavy_split(const Geo G, cons
         for (uint32_t j = 0; j < 4; ++j) q[j] = qn[j];
         ok = okn;
     }
+    for (; zi < zq; zi += zstride) zero[zi] = make_uint4(0u, 0u, 0u, 0u);
     split_flush(bm, kwords, bits_g, &s_cnt, rcount);
 }
 
@@ -471,19 +487,20 @@ Residual residual_layout(const cbaa_tuning &T, uint64_t m, const uint32_t *entri
 
 template <uint32_t THREADS, uint32_t MINB, bool ORIENT>
 cudaError_t launch_split(const Geo &G, const uint32_t *pairs, uint64_t m, const BinWs &W, uint32_t K,
-                         uint32_t kwords, const Residual &R, cudaStream_t s) {
+                         uint32_t kwords, const Residual &R, uint32_t *zero, cudaStream_t s) {
     auto k = k_heavy_split<THREADS, MINB, ORIENT>;
     const size_t smem = sizeof(uint32_t) * ((size_t)kTabWords + kwords);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     k<<<R.nreg, THREADS, smem, s>>>(G, pairs, m, W.heavy.count, W.heavy.key, K, kwords, W.heavy.bits, W.heavy.list,
-                                    W.heavy.ctr, const_cast<uint2 *>(R.entries), R.rcap, W.heavy.rcount());
+                                    W.heavy.ctr, const_cast<uint2 *>(R.entries), R.rcap, W.heavy.rcount(),
+                                    reinterpret_cast<uint4 *>(zero), zero ? G.cube_words / 4 : 0);
     return cudaGetLastError();
 }
 
 template <bool ORIENT>
 cudaError_t heavy_pass(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint64_t m, const BinWs &W,
-                       const cbaa_tuning &T, bool sampled, cudaStream_t s) {
+                       const cbaa_tuning &T, bool sampled, bool zero_cube, cudaStream_t s) {
     const uint32_t K = heavy_sources(G, T);
     const uint32_t kwords = K * G.W;
     const int sms = num_sms();
@@ -502,7 +519,7 @@ cudaError_t heavy_pass(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     Residual R = residual_layout(T, m, W.codes, W.heavy.rcount());
     R.x = HeavyExpand{W.heavy.list, W.heavy.ctr, W.heavy.bits, K};
-    e = launch_split<1024, 1, ORIENT>(G, pairs, m, W, K, kwords, R, s);
+    e = launch_split<1024, 1, ORIENT>(G, pairs, m, W, K, kwords, R, zero_cube ? cube : nullptr, s);
     if (e != cudaSuccess) return e;
     // the residual's row-tile pass in the room after the residual regions
     const uint64_t rw = 2 * (uint64_t)R.nreg * R.rcap;
@@ -521,7 +538,7 @@ bool heavy_enabled(const Geo &G, uint32_t n_cubes, uint64_t n, const cbaa_tuning
 }
 
 cudaError_t launch_update_heavy(const Geo &G, uint32_t *cube, const uint32_t *pairs, uint64_t n, const BinWs &W,
-                                const cbaa_tuning &T, cudaStream_t s) {
+                                const cbaa_tuning &T, cudaStream_t s, bool assign) {
     if (n == 0) return cudaSuccess;
     // Largest pass that fits the code buffer: the residual entries (2 words per
     // packet) and the row-tile pass over them, whose run capacities come from a
@@ -546,10 +563,17 @@ cudaError_t launch_update_heavy(const Geo &G, uint32_t *cube, const uint32_t *pa
     if (sampled && mmax < (T.tile_kind == 3 ? (n < (1u << 16) ? n : (1u << 16)) : counted)) sampled = false;
     if (!sampled) mmax = counted;
     if (mmax == 0) return cudaErrorInvalidValue;       // not reached: a workspace holds A + 2 words per packet
+    if (assign && (G.cube_words & 3u)) {              // not whole 16-byte words: a memset first
+        const cudaError_t e = cudaMemsetAsync(cube, 0, G.cube_words * 4u, s);
+        if (e != cudaSuccess) return e;
+        assign = false;
+    }
     for (uint64_t done = 0; done < n;) {
         const uint64_t m = n - done < mmax ? n - done : mmax;
-        const cudaError_t e = G.n_inner > 0 ? heavy_pass<true>(G, cube, pairs + 2 * done, m, W, T, sampled, s)
-                                            : heavy_pass<false>(G, cube, pairs + 2 * done, m, W, T, sampled, s);
+        // later passes OR into the first one's cube (columns of >= 32 words: whole 16-byte words)
+        const bool zero = assign && done == 0;
+        const cudaError_t e = G.n_inner > 0 ? heavy_pass<true>(G, cube, pairs + 2 * done, m, W, T, sampled, zero, s)
+                                            : heavy_pass<false>(G, cube, pairs + 2 * done, m, W, T, sampled, zero, s);
         if (e != cudaSuccess) return e;
         done += m;
     }

@@ -112,6 +112,41 @@ def test_heavy_split_fewer_blocks(C, oracle, win, split_blocks):
     assert np.array_equal(got, oracle.build_cube(d, pairs))
 
 
+@pytest.mark.parametrize("tuning,ws_div", [(dict(heavy=3, tile_kind=3), 1),
+                                           (dict(heavy=3, tile_kind=3, split_blocks=37), 1),
+                                           (dict(heavy=3, tile_kind=0), 5),
+                                           (dict(heavy=1, tile_kind=2), 1),
+                                           (dict(heavy=1, tile_kind=1), 1)])
+@pytest.mark.parametrize("win", ["4m", "tiny"])
+def test_assign_update_replaces_a_dirty_cube(C, oracle, win, tuning, ws_div):
+    """cbaa_cube_update_binned_assign on a cube full of random words: the cube must become the
+    oracle's cube of these packets alone -- zeroed by the split's blocks on the heavy path (one
+    block per SM, 37 blocks, several passes), by a memset on the row-tile and column-tile paths."""
+    d = GEO.L2
+    pairs = pairs_of(win)
+    before = C.get_tuning()
+    try:
+        C.set_tuning(**{**before, **tuning})
+        cube = C.Cube(d)
+        rng = np.random.default_rng(17)
+        cube.load_numpy(rng.integers(0, 2**32, size=cube.nbytes // 4, dtype=np.uint64).astype(np.uint32))
+        ws = C.UpdateWorkspace(d, max(1, pairs.shape[0] // ws_div))
+        cube.update_binned(dev_pairs(pairs), ws, assign=True)
+        got = cube.to_numpy()
+    finally:
+        C.set_tuning(**before)
+    assert np.array_equal(got, oracle.build_cube(d, pairs))
+
+
+def test_assign_update_of_no_packets_zeroes_the_cube(C):
+    d = GEO.L2
+    cube = C.Cube(d)
+    cube.load_numpy(np.full(cube.nbytes // 4, 0xFFFFFFFF, dtype=np.uint32))
+    ws = C.UpdateWorkspace(d, 1024)
+    cube.update_binned(dev_pairs(np.zeros((0, 2), np.uint32)), ws, n=0, assign=True)
+    assert not cube.to_numpy().any()
+
+
 @pytest.mark.parametrize("heavy", [2, 3])
 def test_heavy_split_skewed(C, oracle, heavy):
     """Half the packets one pair and a fifth one source to many peers (one source dominates the
