@@ -135,3 +135,13 @@ def test_multi_workspace_limits(C):
     assert C.update_multi_workspace_bytes(GEO.L2, 9, 1 << 20) == 0        # 9 x 64 MiB > 512 MiB
     assert C.update_multi_workspace_bytes(GEO.TINY, 16, 1 << 10) > 0
     assert C.update_multi_workspace_bytes(GEO.TINY, 17, 1 << 10) == 0
+
+
+def test_update_entry_points_reject_a_null_cube_before_any_device_work(C):
+    """Argument checks that come before anything is enqueued (no device is touched): a null cube,
+    for the plain, the partitioned and the assigning partitioned update."""
+    lib = C.lib()
+    assert lib.cbaa_cube_update(None, None, 1, None) == C.ERR_INVALID_ARG
+    assert lib.cbaa_cube_update_binned(None, None, 1, None, 0, None) == C.ERR_INVALID_ARG
+    assert lib.cbaa_cube_update_binned_assign(None, None, 1, None, 0, None) == C.ERR_INVALID_ARG
+    assert lib.cbaa_cube_update_binned_assign(None, None, 0, None, 0, None) == C.ERR_INVALID_ARG
